@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Throughput of the Fourier split-operator step on GB300.
+
+One benchmark step is one full propagation of the 2D Schroedinger workload
+(2048 x 2048 lattice on [-200, 200)^2, complex64, soft-core Coulomb potential,
+sin^2 laser pulse, 5000 split steps of dt = 0.02) through ``sop_step``, with
+psi and V resident in HBM.  The metric is grid-point-steps per second
+(lattice points x split steps / device time), whole job over all GPUs.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+
+Under torchrun each rank propagates its own replica (independent problems;
+the split step has no cross-GPU exchange), ranks are timed between barriers
+and the maximum time is used.  ``--impl reference`` times the FP64 CPU oracle
+on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-pt-steps/s and HBM-roofline % per split step, FP32 vs FP64 at stated err"
+UNIT = "grid-pt-steps/s"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10, help="timed benchmark steps")
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--split-steps", type=int, default=5000, help="split steps per benchmark step")
+    ap.add_argument("--n", type=int, default=2048, help="lattice side")
+    ap.add_argument("--fp64-steps", type=int, default=500, help="split steps of the FP64 sample (0: skip)")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="benchmark steps of the end-to-end leg (0: skip)")
+    ap.add_argument("--cpu-steps", type=int, default=12, help="oracle split steps of the CPU baseline (0: skip)")
+    ap.add_argument("--ref-split-steps", type=int, default=2, help="oracle split steps per reference step")
+    ap.add_argument("--json-out", default=None)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_1012_3911_gb300", "csrc")
+    for name in sorted(os.listdir(cs)):
+        with open(os.path.join(cs, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_class: str):
+    """Per-launch DRAM bytes of a pass class from the committed ncu summary,
+    or None when the kernels changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    ent = d.get("per_launch_dram_bytes", {}).get(kernel_class)
+    return None if ent is None else float(ent)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.proc = None
+        self.bus_id = bus_id
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.bus_id:
+            cmd += ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_reference(args, rank, world):
+    """The FP64 oracle on the host cores, bounded sample per step."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1012_3911_gb300 import workloads as wl
+    oracle.build()
+    cores = oracle.max_threads()
+    oracle.set_threads(cores)
+    w = wl.config2(n=args.n, n_steps=args.split_steps)
+    S = args.ref_split_steps
+    F = w.field[:S]
+    psi = w.psi0
+    for _ in range(args.warmup):
+        oracle.schrodinger_propagate(psi, w.V, w.spacing, w.dt, S, F)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.schrodinger_propagate(psi, w.V, w.spacing, w.dt, S, F)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = w.npoints * S * args.steps / total
+    sample = (f"{S} of {w.n_steps} split steps per benchmark step on the full {args.n}x{args.n} lattice, "
+              f"FP64 oracle, {cores} threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded, paper-shaped)",
+        "config": {"workload": f"2D Schroedinger {args.n}x{args.n}, soft-core V, sin^2 laser along x, dt=0.02",
+                   "split_steps_per_step": S, "parallelism": "host cores (OpenMP over pencils)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    assert torch.cuda.is_available(), "bench.py needs a CUDA GPU"
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = tdist
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    from paper_1012_3911_gb300 import build as sop_build
+    sop_build.build()
+    from paper_1012_3911_gb300 import sop, workloads as wl
+
+    w = wl.config2(n=args.n, n_steps=args.split_steps)
+    S = args.split_steps
+    stream = torch.cuda.current_stream()
+    prop = sop.Propagator(w.dims, w.spacing, 1, "c64")
+    psi0 = torch.from_numpy(w.psi0.astype(np.complex64)).cuda()
+    prop.set_potential(w.V)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def one_step(ev=None):
+        prop.state.copy_(psi0)          # same input every benchmark step (untimed)
+        flush.fill_(1.0)                # evict L2 (untimed)
+        if ev is not None:
+            ev[0].record(stream)
+        prop.step(S, w.dt, w.field)
+        if ev is not None:
+            ev[1].record(stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    barrier()
+
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(local).pci_bus_id  # type: ignore[attr-defined]
+    except Exception:
+        bus = None
+    sampler = ClockSampler(bus)
+    sop.sop_profile_enable(prop.plan, True)
+    sop.sop_profile_read(prop.plan)
+    launches0 = sop.sop_launch_counter(prop.plan)
+    events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    sampler.start()
+    barrier()
+    for k in range(args.steps):
+        one_step(events[k])
+    barrier()
+    clocks = sampler.stop()
+    launches = sop.sop_launch_counter(prop.plan) - launches0
+    cls_ms, cls_n = sop.sop_profile_read(prop.plan)
+    sop.sop_profile_enable(prop.plan, False)
+    total_ms = sum(a.elapsed_time(b) for a, b in events)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * w.npoints * S * args.steps / (total_ms * 1e-3)
+
+    # ---- roofline of the dominant kernel -----------------------------------
+    names = sop.PASS_CLASS_NAMES
+    dom = int(np.argmax(cls_ms[:2]))
+    bytes_per_pt = {0: 2 * 8 + 4, 1: 2 * 8}[dom]   # psi read+write (+ FP32 V on the real-space side)
+    alg_bytes = w.npoints * bytes_per_pt
+    avg_ms = cls_ms[dom] / max(1, cls_n[dom])
+    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": ncu_traffic(names[dom]), "kernel": names[dom], "peak_source": peak_kind,
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
+                "pass_ms_share": {names[i]: cls_ms[i] / max(1e-12, sum(cls_ms)) for i in range(len(cls_ms)) if cls_n[i]}}
+
+    # ---- FP64 sample, same lattice -----------------------------------------
+    fp64 = None
+    if args.fp64_steps > 0:
+        p64 = sop.Propagator(w.dims, w.spacing, 1, "c128")
+        p64.set_potential(w.V)
+        psi64 = torch.from_numpy(w.psi0).cuda()
+        S64 = args.fp64_steps
+        ts = []
+        for k in range(3):
+            p64.state.copy_(psi64)
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            p64.step(S64, w.dt, w.field[:S64])
+            b.record(stream)
+            torch.cuda.synchronize()
+            if k > 0:
+                ts.append(a.elapsed_time(b))
+        ms = sum(ts) / len(ts)
+        fp64 = {"value": w.npoints * S64 / (ms * 1e-3), "unit": UNIT, "split_steps": S64,
+                "ms_per_split_step": ms / S64, "dtype": "f64"}
+        p64.close()
+
+    # ---- end to end through the C ABI with host buffers ------------------------
+    e2e = None
+    if args.e2e_steps > 0:
+        host = torch.from_numpy(w.psi0.astype(np.complex64)).pin_memory()
+        src = host.clone()
+        ts = []
+        for k in range(args.e2e_steps + 1):
+            host.copy_(src)
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            prop.step_host(host, S, w.dt, w.field)
+            t1 = time.perf_counter()
+            if k > 0:
+                ts.append(t1 - t0)
+        nbytes = host.numel() * host.element_size()
+        e2e = {"value": world * w.npoints * S / (sum(ts) / len(ts)), "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    # ---- oracle on the host cores (rank 0) and accuracy on that sample -------
+    cpu = None
+    err = None
+    if rank == 0 and args.cpu_steps > 0:
+        import oracle
+        oracle.build()
+        cores = oracle.max_threads()
+        oracle.set_threads(cores)
+        nc = args.cpu_steps
+        t0 = time.perf_counter()
+        ref = oracle.schrodinger_propagate(w.psi0, w.V, w.spacing, w.dt, nc, w.field[:nc])
+        tcpu = time.perf_counter() - t0
+        cpu = {"value": w.npoints * nc / tcpu, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{nc} of {S} split steps on the full {args.n}x{args.n} lattice (FP64, {tcpu:.1f} s)"}
+        err = {"split_steps": nc}
+        for dt_name in ("c64", "c128"):
+            p = sop.Propagator(w.dims, w.spacing, 1, dt_name)
+            p.set_potential(w.V)
+            p.set_state(torch.from_numpy(w.psi0))
+            p.step(nc, w.dt, w.field[:nc])
+            out = p.state.cpu().numpy().astype(np.complex128)
+            err[{"c64": "f32", "c128": "f64"}[dt_name]] = float(np.linalg.norm(out - ref) / np.linalg.norm(ref))
+            p.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded, shaped like the paper's 2D laser-driven soft-core workload)",
+            "config": {"workload": f"2D Schroedinger {args.n}x{args.n} on [-200,200)^2, complex64, soft-core V, "
+                                   f"sin^2 laser along x, {S} split steps of dt=0.02 per benchmark step",
+                       "lattice": [args.n, args.n], "split_steps_per_step": S,
+                       "ms_per_split_step": total_ms / args.steps / S,
+                       "l2": "flushed (256 MiB write) before every timed step; psi + V tables stay L2-resident "
+                             "within a step",
+                       "parallelism": f"replicas x{world} (independent problems, no data-path collective)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "fp64": fp64, "err_vs_oracle": err, "clocks": clocks,
+        }
+        s = json.dumps(line)
+        print(s, flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                f.write(s + "\n")
+    prop.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+/*
+ * sop.h -- C ABI of libsop.so, a GB300 (sm_103a) Fourier split-operator
+ * propagator for the time-dependent Schroedinger equation (scalar psi) and
+ * the Dirac equation (four-component spinor) on periodic 1D/2D/3D lattices.
+ *
+ * One time step of size tau is the second-order Strang factorisation of
+ * Bauke & Keitel (arXiv:1012.3911), Eqs. 6-8:
+ *     psi <- U_A1(1/2) F^-1 U~_A2(1) F U_A1(1/2) psi
+ * with the Schroedinger split of Eqs. 10a/10b (real-space factor Eq. 11,
+ * momentum-space factor Eq. 13) and the Dirac split of Eqs. 18a/18b
+ * (real-space factor Eqs. 21-26, momentum-space factor Eqs. 27-33).
+ *
+ * Conventions (all calls):
+ *   - Units are set by sop_params (default: atomic units, electron:
+ *     mass 1, charge -1, hbar 1, c 137.036).
+ *   - Lattice: axis a has dims[a] points with spacing spacing[a];
+ *     x_{a,j} = -dims[a]*spacing[a]/2 + j*spacing[a] (the box [-L/2, L/2)).
+ *     Momenta p_{a,k} = hbar*2*pi*kappa/(dims[a]*spacing[a]) with kappa = k
+ *     for 2k < dims[a], else k - dims[a].
+ *   - Layout: psi is interleaved complex (complex64 = 2 x float, or
+ *     complex128 = 2 x double) in C order with axis 0 (x) fastest:
+ *     psi[c][z][y][x]; components c are contiguous blocks of prod(dims)
+ *     points.  dims[0] = n_x.
+ *   - Fields: field_samples holds n_steps rows of ndim doubles, the field at
+ *     the midpoint t_n + tau/2 of each step, components in axis order.  For
+ *     Schroedinger it is the electric field E in the length gauge (the scalar
+ *     potential gains -q x.E); for Dirac it is the uniform vector potential A
+ *     of Eq. 18a.  NULL means no field.
+ *   - Every call returns a sop_status.  Nothing throws across the ABI.  On a
+ *     non-zero status, sop_last_error() returns a thread-local message.
+ *   - Ownership: the plan owns its tables and scratch (device memory it
+ *     allocates at create time or on first use); the caller owns psi and V.
+ *   - Streams: all device work of a plan is enqueued on the CUDA stream
+ *     given at create time (NULL: the legacy default stream).  sop_step is
+ *     asynchronous; sop_norm, sop_energy and sop_step_host synchronise that
+ *     stream.
+ */
+#ifndef SOP_H
+#define SOP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sop_plan_s *sop_plan;
+
+typedef enum { SOP_C64 = 0, SOP_C128 = 1 } sop_dtype;
+
+typedef enum {
+    SOP_OK = 0,
+    SOP_EINVAL = -1,          /* bad argument (null pointer, bad size, misaligned pointer) */
+    SOP_EUNSUPPORTED = -2,    /* valid but not supported (side not 2^a*3^b in [8,4096], ...) */
+    SOP_ENOMEM = -3,          /* device allocation failed */
+    SOP_ECUDA = -4,           /* a CUDA call failed; the message names it */
+    SOP_ETIMEOUT = -5,        /* reserved for bounded device-side waits */
+    SOP_ESTATE = -6           /* call out of order (e.g. stepping before a state is bound) */
+} sop_status;
+
+/* Physical constants; pass NULL to sop_plan_create for atomic units and an
+ * electron (mass 1, charge -1, hbar 1, c 137.036). */
+typedef struct {
+    double mass;
+    double charge;
+    double hbar;
+    double c;
+} sop_params;
+
+/* Create a plan for one lattice (Sec. 2.1: a regular rectangular lattice
+ * of N points on which the Fourier transform becomes a DFT).
+ *   out        receives the plan handle.
+ *   ndim       1, 2 or 3.
+ *   dims       ndim sides in axis order (dims[0] = n_x, contiguous); each
+ *              side must be 2^a * 3^b with a >= 2, b <= 1 and 8 <= side <= 4096.
+ *   spacing    ndim lattice spacings (> 0).
+ *   components 1 (Schroedinger, Sec. 2.2) or 4 (Dirac, Sec. 2.3, ndim = 2).
+ *   dtype      SOP_C64 (FP32 arithmetic, phase and twiddle tables formed in
+ *              FP64 and rounded) or SOP_C128 (FP64 throughout).
+ *   params     NULL or the physical constants.
+ *   cuda_stream  a cudaStream_t (as void*) or NULL.
+ * Allocates the plan's twiddle tables, reduction scratch and field-table
+ * buffers on the current device.  Returns SOP_EINVAL, SOP_EUNSUPPORTED,
+ * SOP_ENOMEM or SOP_ECUDA on failure (then *out is NULL). */
+int sop_plan_create(sop_plan *out, int ndim, const int64_t *dims, const double *spacing,
+                    int components, int dtype, const sop_params *params, void *cuda_stream);
+
+/* Free every device buffer the plan owns.  Waits for the plan's stream.
+ * Accepts NULL. */
+int sop_plan_destroy(sop_plan plan);
+
+/* Bind the wave function: psi_dev is a device pointer to components *
+ * prod(dims) complex values of the plan's dtype, aligned to the complex
+ * size.  The plan borrows it; the caller keeps it alive while the plan
+ * steps.  sop_step updates it in place. */
+int sop_bind_state(sop_plan plan, void *psi_dev);
+
+/* Set the potential energy V (= q*phi of Eqs. 10a/18a, without the laser
+ * term) from a device array of prod(dims) reals, FP64 if v_is_fp64 else
+ * FP32.  The plan copies it (FP64) and rebuilds the phase tables
+ * exp(-i V tau/(2 hbar)) and exp(-i V tau/hbar) at the next sop_step.
+ * A plan whose potential was never set uses V = 0. */
+int sop_set_potential(sop_plan plan, const void *V_dev, int v_is_fp64);
+
+/* Advance the bound state by n_steps Strang steps of size dt (Eq. 8).  The
+ * real-space factors of adjacent steps are merged (exact algebra): the call
+ * applies one half real-space factor at its start and one at its end.
+ * field_samples: host array of n_steps*ndim doubles or NULL (see above).
+ * Asynchronous on the plan stream.  n_steps = 0 is a no-op.  Returns
+ * SOP_ESTATE if no state is bound. */
+int sop_step(sop_plan plan, int64_t n_steps, double dt, const double *field_samples);
+
+/* As sop_step, for a wave function in HOST memory: copies psi_host (same
+ * layout and dtype as the bound state) to the bound device buffer, steps,
+ * copies the result back into psi_host and synchronises the stream.  The
+ * host->device and device->host copies are inside the call (the paper's
+ * "overall time including transfers", Sec. 4.2).  psi_host may be pinned or
+ * pageable. */
+int sop_step_host(sop_plan plan, void *psi_host, int64_t n_steps, double dt,
+                  const double *field_samples);
+
+/* *out = dV * sum over points and components of |psi|^2, accumulated in
+ * FP64 (dV = product of spacings).  Synchronises the plan stream. */
+int sop_norm(sop_plan plan, double *out);
+
+/* *out = field-free energy <T> + <V> of the bound state, accumulated in
+ * FP64: <V> = dV sum_j V_j |psi_j|^2 and <T> = (dV/N) sum_k psi~_k^dag T(p_k) psi~_k
+ * with T = |p|^2/(2m) (Schroedinger) or c alpha.p + m c^2 beta (Dirac, Eq. 28).
+ * Uses a plan-owned scratch copy of psi (allocated on first use).
+ * Synchronises the plan stream. */
+int sop_energy(sop_plan plan, double *out);
+
+/* Per-pass device timing with CUDA events on the plan stream.  While
+ * enabled, sop_step records an event pair around every kernel it launches.
+ * sop_profile_read synchronises the stream and returns, per pass class,
+ * the summed device milliseconds and the launch count since profiling was
+ * enabled (arrays of max_classes entries, SOP_PASS_CLASSES at most); it
+ * also resets the counters.  Classes: 0 real-space axis pass, 1 momentum-
+ * space (last axis) pass, 2 middle-axis transform pass, 3 one-dimensional
+ * whole-step kernel, 4 table set-up kernels. */
+#define SOP_PASS_CLASSES 5
+int sop_profile_enable(sop_plan plan, int on);
+int sop_profile_read(sop_plan plan, double *ms, int64_t *launches, int max_classes);
+
+/* Total number of kernels this plan has launched since it was created
+ * (passes, table set-up and reductions).  Host-side counter; no sync. */
+int64_t sop_launch_counter(sop_plan plan);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *sop_last_error(void);
+
+/* ABI version (incremented on incompatible changes). */
+int sop_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SOP_H */

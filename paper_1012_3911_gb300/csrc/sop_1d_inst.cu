@@ -1,0 +1,79 @@
+// sop_1d_inst.cu -- instantiates the one-dimensional whole-step kernel for
+// one dtype (-DSOP_REAL=float|double, with -DSOP_IS_DOUBLE=1 for double); the
+// double build also defines the pass-geometry query and the shared-memory
+// attribute helper.
+#include <mutex>
+#include <set>
+#include <utility>
+
+#include "sop_kernels.cuh"
+
+#ifndef SOP_REAL
+#error "SOP_REAL must be defined"
+#endif
+
+#define SOP_SIZES(X) \
+    X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024) \
+    X(1536) X(2048) X(3072) X(4096)
+
+namespace sop {
+
+#if SOP_IS_DOUBLE
+cudaError_t launch_1d_f64(const Args1D &a, int n, cudaStream_t s) {
+#else
+cudaError_t launch_1d_f32(const Args1D &a, int n, cudaStream_t s) {
+#endif
+    switch (n) {
+#define SOP_CASE(N) \
+    case N:         \
+        return launch_1d_t<SOP_REAL, N>(a, s);
+        SOP_SIZES(SOP_CASE)
+#undef SOP_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+#if SOP_IS_DOUBLE
+namespace {
+template <typename Real, int N> void geom_of(int nc, bool contig, int *th, int *wp, int *sm) {
+    if (nc == 1) {
+        if (contig) { using C = PassCfg<Real, N, 1, true>; *th = C::THREADS; *wp = C::WP; *sm = (int)C::SMEM; }
+        else { using C = PassCfg<Real, N, 1, false>; *th = C::THREADS; *wp = C::WP; *sm = (int)C::SMEM; }
+    } else {
+        if (contig) { using C = PassCfg<Real, N, 2, true>; *th = C::THREADS; *wp = C::WP; *sm = (int)C::SMEM; }
+        else { using C = PassCfg<Real, N, 2, false>; *th = C::THREADS; *wp = C::WP; *sm = (int)C::SMEM; }
+    }
+}
+}  // namespace
+
+bool pass_geometry(bool f64, int n, int nc, bool contig, int *threads, int *pencils_per_cta, int *smem) {
+    switch (n) {
+#define SOP_CASE(N)                                                                          \
+    case N:                                                                                  \
+        if (f64) geom_of<double, N>(nc, contig, threads, pencils_per_cta, smem);             \
+        else geom_of<float, N>(nc, contig, threads, pencils_per_cta, smem);                  \
+        return true;
+        SOP_SIZES(SOP_CASE)
+#undef SOP_CASE
+        default:
+            return false;
+    }
+}
+
+cudaError_t ensure_smem_attr(const void *kern, int bytes) {
+    // The attribute is per function and device; remember which pairs are set.
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({kern, dev})) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.insert({kern, dev});
+    return e;
+}
+#endif
+
+}  // namespace sop

@@ -1,0 +1,748 @@
+// sop_api.cu -- the sop_* C ABI: plans, table management and the split-step
+// time loop of Bauke & Keitel (arXiv:1012.3911), Eq. 8.
+//
+// Time loop of one sop_step call with n steps (d >= 2, x = axis 0):
+//   real-space index P = 0..n: pass over x with
+//       [inverse FFT_x if P > 0] -> U_A1 -> [forward FFT_x if P < n]
+//     where U_A1 is the half factor for P = 0 and P = n and the product of
+//     the trailing half of step P-1 and the leading half of step P otherwise;
+//   after every P < n, the momentum-space side of step P:
+//       2D: pass over y: forward FFT_y -> U~_A2 / N -> inverse FFT_y
+//       3D: forward FFT_y; pass over z: forward FFT_z -> U~_A2 / N -> inverse FFT_z;
+//           inverse FFT_y
+// so a 2D step costs two passes over psi and a 3D step four.  In 1D a single
+// kernel keeps the line on chip for many steps.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sop.h"
+#include "sop_internal.h"
+
+using namespace sop;
+using cd = std::complex<double>;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(SOP_ECUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr int64_t kFieldChunk = 512;   // real-space indices per field-table chunk
+
+struct EventPair {
+    cudaEvent_t a, b;
+    int cls;
+};
+
+}  // namespace
+
+struct sop_plan_s {
+    int ndim = 0;
+    int64_t dims[3] = {1, 1, 1};
+    double h[3] = {1, 1, 1};
+    int comps = 1;
+    bool f64 = false;
+    sop_params prm{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int64_t npts = 0;
+    size_t csz = 0;
+
+    void *psi = nullptr;
+    double *V = nullptr;
+    bool v_set = false;
+
+    void *tw[3] = {nullptr, nullptr, nullptr};
+    void *vhalf = nullptr, *vfull = nullptr;
+    void *kin[3] = {nullptr, nullptr, nullptr};
+    void *dtab = nullptr;
+    double *theta = nullptr;        // device scratch for per-axis angles
+    double tables_dt = std::nan("");
+    bool tables_valid = false;
+    double scale_hi = 1.0, scale_lo = 0.0;
+
+    void *ftab = nullptr;           // kFieldChunk rows x row_len
+    int64_t row_len = 0;
+    int64_t foff[3] = {0, 0, 0};
+    double *fvec = nullptr;         // device field vectors, (n+1) x ndim
+    int64_t fvec_cap = 0;
+    double *host_stage = nullptr;   // pinned staging buffer
+    int64_t host_stage_cap = 0;
+    cudaEvent_t stage_done = nullptr;
+
+    double *partial = nullptr;
+    double *result = nullptr;
+    double *host_result = nullptr;  // pinned, 4 doubles
+    double *pgrid = nullptr;
+    void *scratch = nullptr;
+
+    bool prof = false;
+    std::vector<EventPair> events;
+    std::vector<cudaEvent_t> event_pool;
+    int64_t launches = 0;
+};
+
+namespace {
+
+bool is_finite(double x) { return std::isfinite(x); }
+
+template <typename T> int dalloc(T **p, size_t bytes, const char *what) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? SOP_ENOMEM : SOP_ECUDA,
+                    std::string("cudaMalloc(") + what + ", " + std::to_string(bytes) + " bytes): " + cudaGetErrorString(e));
+    }
+    return SOP_OK;
+}
+
+void dfree(void *p) {
+    if (p) cudaFree(p);
+}
+
+double lattice_p(int64_t n, double h, int64_t k, double hbar) {
+    const int64_t kap = (2 * k < n) ? k : k - n;
+    return hbar * kTwoPi * (double)kap / ((double)n * h);
+}
+
+cudaEvent_t take_event(sop_plan p) {
+    if (!p->event_pool.empty()) {
+        cudaEvent_t e = p->event_pool.back();
+        p->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch bracket: counts launches and, when profiling, records events.
+struct Bracket {
+    sop_plan p;
+    int cls;
+    cudaEvent_t a = nullptr;
+    Bracket(sop_plan pp, int c) : p(pp), cls(c) {
+        if (p->prof) {
+            a = take_event(p);
+            cudaEventRecord(a, p->stream);
+        }
+    }
+    void done(int nlaunch = 1) {
+        p->launches += nlaunch;
+        if (p->prof) {
+            cudaEvent_t b = take_event(p);
+            cudaEventRecord(b, p->stream);
+            p->events.push_back({a, b, cls});
+        }
+    }
+};
+
+int ensure_stage(sop_plan p, int64_t doubles) {
+    if (p->host_stage_cap >= doubles) {
+        // the previous upload must have left the staging buffer
+        cudaError_t e = cudaEventSynchronize(p->stage_done);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        return SOP_OK;
+    }
+    if (p->host_stage) {
+        cudaEventSynchronize(p->stage_done);
+        cudaFreeHost(p->host_stage);
+        p->host_stage = nullptr;
+    }
+    int64_t cap = doubles < 4096 ? 4096 : doubles;
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&p->host_stage), (size_t)cap * sizeof(double),
+                                  cudaHostAllocDefault);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaHostAlloc");
+    p->host_stage_cap = cap;
+    return SOP_OK;
+}
+
+// Upload n doubles through the pinned staging buffer to dst (async).
+int upload(sop_plan p, double *dst, const double *src, int64_t n) {
+    int rc = ensure_stage(p, n);
+    if (rc) return rc;
+    std::memcpy(p->host_stage, src, (size_t)n * sizeof(double));
+    cudaError_t e = cudaMemcpyAsync(dst, p->host_stage, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(upload)");
+    cudaEventRecord(p->stage_done, p->stream);
+    return SOP_OK;
+}
+
+int plan_free(sop_plan p) {
+    if (!p) return SOP_OK;
+    cudaStreamSynchronize(p->stream);
+    for (int a = 0; a < 3; ++a) {
+        dfree(p->tw[a]);
+        dfree(p->kin[a]);
+    }
+    dfree(p->V);
+    dfree(p->vhalf);
+    dfree(p->vfull);
+    dfree(p->dtab);
+    dfree(p->theta);
+    dfree(p->ftab);
+    dfree(p->fvec);
+    dfree(p->partial);
+    dfree(p->result);
+    dfree(p->pgrid);
+    dfree(p->scratch);
+    if (p->host_stage) cudaFreeHost(p->host_stage);
+    if (p->host_result) cudaFreeHost(p->host_result);
+    if (p->stage_done) cudaEventDestroy(p->stage_done);
+    for (auto &ep : p->events) {
+        cudaEventDestroy(ep.a);
+        cudaEventDestroy(ep.b);
+    }
+    for (auto e : p->event_pool) cudaEventDestroy(e);
+    delete p;
+    return SOP_OK;
+}
+
+cudaError_t launch_pass(sop_plan p, const PassArgs &a, int nc) {
+    const bool contig = a.axis == 0;
+    if (p->f64) return contig ? launch_pass_f64_contig(a, nc, p->stream) : launch_pass_f64_strided(a, nc, p->stream);
+    return contig ? launch_pass_f32_contig(a, nc, p->stream) : launch_pass_f32_strided(a, nc, p->stream);
+}
+
+void base_args(sop_plan p, PassArgs &a, void *psi, int axis) {
+    std::memset(&a, 0, sizeof(a));
+    a.psi = psi;
+    a.comp_stride = p->npts;
+    a.n_pencils = p->npts / p->dims[axis];
+    a.n_batch = 1;
+    int64_t stride = 1;
+    for (int b = 0; b < axis; ++b) stride *= p->dims[b];
+    a.stride = stride;
+    a.ndim = p->ndim;
+    a.axis = axis;
+    for (int b = 0; b < 3; ++b) a.dims[b] = b < p->ndim ? p->dims[b] : 1;
+    a.tw = p->tw[axis];
+    a.scale_hi = p->scale_hi;
+    a.scale_lo = p->scale_lo;
+    a.pair_comp[0][0] = 0;
+    a.pair_comp[0][1] = 3;
+    a.pair_comp[1][0] = 1;
+    a.pair_comp[1][1] = 2;
+}
+
+int run_pass(sop_plan p, const PassArgs &a, int nc, int cls, const char *what) {
+    Bracket br(p, cls);
+    cudaError_t e = launch_pass(p, a, nc);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    br.done();
+    return SOP_OK;
+}
+
+// Rebuild the tables that depend on the time step (and V).
+int ensure_tables(sop_plan p, double dt) {
+    if (p->tables_valid && p->tables_dt == dt) return SOP_OK;
+    const double hbar = p->prm.hbar;
+    cudaError_t e;
+    if (p->v_set) {
+        Bracket br(p, 4);
+        e = build_vphase(p->vhalf, p->V, p->npts, 0.5 * dt / hbar, p->f64, p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "build_vphase(half)");
+        e = build_vphase(p->vfull, p->V, p->npts, dt / hbar, p->f64, p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "build_vphase(full)");
+        br.done(2);
+    }
+    if (p->comps == 1) {
+        // Separable kinetic factor exp(-i tau p_a^2 / (2 m hbar)) per axis (Eq. 13, A = 0).
+        std::vector<double> th;
+        for (int a = 0; a < p->ndim; ++a)
+            for (int64_t k = 0; k < p->dims[a]; ++k) {
+                const double pk = lattice_p(p->dims[a], p->h[a], k, hbar);
+                th.push_back(dt * pk * pk / (2.0 * p->prm.mass * hbar));
+            }
+        int rc = upload(p, p->theta, th.data(), (int64_t)th.size());
+        if (rc) return rc;
+        Bracket br(p, 4);
+        int64_t off = 0;
+        for (int a = 0; a < p->ndim; ++a) {
+            e = build_axis_phase(p->kin[a], p->theta + off, (int)p->dims[a], p->f64, p->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "build_axis_phase");
+            off += p->dims[a];
+        }
+        br.done(p->ndim);
+    } else {
+        Bracket br(p, 4);
+        e = build_dirac_table(p->dtab, p->dims, p->h, p->prm.mass, p->prm.c, hbar, dt, p->f64, p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "build_dirac_table");
+        br.done();
+    }
+    p->tables_dt = dt;
+    p->tables_valid = true;
+    return SOP_OK;
+}
+
+// 2x2 blocks of the half-step spinor-mixing factor (Eq. 26 with delta = 1/2,
+// Abar = A tau) on the component pairs (1,4) and (2,3) of a 2D spinor:
+//   R = cos(theta) + i sin(theta) sum_i n_i alpha_i,  theta = q c |A| tau / (2 hbar),
+// where sum_i n_i alpha_i is [[0, n_x - i n_y],[n_x + i n_y, 0]] on (1,4) and
+// [[0, n_x + i n_y],[n_x - i n_y, 0]] on (2,3).
+void mixing_blocks(const sop_plan p, const double *A, double dt, cd R[2][2][2]) {
+    double ax = 0, ay = 0;
+    if (A) {
+        ax = A[0] * dt;
+        ay = A[1] * dt;
+    }
+    const double amag = std::sqrt(ax * ax + ay * ay);
+    const double theta = 0.5 * p->prm.charge * p->prm.c * amag / p->prm.hbar;
+    const double co = std::cos(theta), si = std::sin(theta);
+    const double nx = amag > 0 ? ax / amag : 0.0, ny = amag > 0 ? ay / amag : 0.0;
+    const cd I(0, 1);
+    for (int pr = 0; pr < 2; ++pr) {
+        const cd up = pr == 0 ? cd(nx, -ny) : cd(nx, ny);
+        const cd lo = pr == 0 ? cd(nx, ny) : cd(nx, -ny);
+        R[pr][0][0] = co;
+        R[pr][0][1] = I * si * up;
+        R[pr][1][0] = I * si * lo;
+        R[pr][1][1] = co;
+    }
+}
+
+int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
+    if (!p) return fail(SOP_EINVAL, "sop_step: null plan");
+    if (!p->psi) return fail(SOP_ESTATE, "sop_step: no state bound (call sop_bind_state first)");
+    if (n < 0) return fail(SOP_EINVAL, "sop_step: n_steps < 0");
+    if (!is_finite(dt)) return fail(SOP_EINVAL, "sop_step: dt is not finite");
+    if (n == 0) return SOP_OK;
+    if (field)
+        for (int64_t i = 0; i < n * p->ndim; ++i)
+            if (!is_finite(field[i])) return fail(SOP_EINVAL, "sop_step: field sample is not finite");
+    int rc = ensure_tables(p, dt);
+    if (rc) return rc;
+
+    const int nd = p->ndim;
+    const double hbar = p->prm.hbar;
+    auto sample = [&](int64_t s, int a) -> double {
+        return (field && s >= 0 && s < n) ? field[s * nd + a] : 0.0;
+    };
+
+    if (p->comps == 4) {
+        // ---- Dirac, 2D, component pairs ------------------------------------
+        for (int64_t P = 0; P <= n; ++P) {
+            PassArgs a;
+            base_args(p, a, p->psi, 0);
+            a.pre = P > 0 ? +1 : 0;
+            a.post = P < n ? -1 : 0;
+            a.op = OP_DV;
+            a.vtab = p->v_set ? ((P == 0 || P == n) ? p->vhalf : p->vfull) : nullptr;
+            cd Rn[2][2][2], Rp[2][2][2];
+            double An[2] = {sample(P, 0), sample(P, 1)};
+            double Ap[2] = {sample(P - 1, 0), sample(P - 1, 1)};
+            mixing_blocks(p, (field && P < n) ? An : nullptr, dt, Rn);
+            mixing_blocks(p, (field && P > 0) ? Ap : nullptr, dt, Rp);
+            for (int pr = 0; pr < 2; ++pr) {
+                // M = R(A_P) R(A_{P-1}): trailing half of step P-1 first.
+                cd M[2][2];
+                for (int i = 0; i < 2; ++i)
+                    for (int j = 0; j < 2; ++j) M[i][j] = Rn[pr][i][0] * Rp[pr][0][j] + Rn[pr][i][1] * Rp[pr][1][j];
+                for (int i = 0; i < 2; ++i)
+                    for (int j = 0; j < 2; ++j) {
+                        a.mix[pr][2 * (2 * i + j)] = M[i][j].real();
+                        a.mix[pr][2 * (2 * i + j) + 1] = M[i][j].imag();
+                    }
+            }
+            rc = run_pass(p, a, 2, 0, "Dirac real-space pass");
+            if (rc) return rc;
+            if (P < n) {
+                PassArgs k;
+                base_args(p, k, p->psi, 1);
+                k.pre = -1;
+                k.post = +1;
+                k.op = OP_DT;
+                k.dtab = p->dtab;
+                rc = run_pass(p, k, 2, 1, "Dirac momentum-space pass");
+                if (rc) return rc;
+            }
+        }
+        return SOP_OK;
+    }
+
+    // ---- Schroedinger -------------------------------------------------------
+    // Field vectors of the real-space factors: f_P = -q tau/(2 hbar) (E_{P-1} + E_P),
+    // the laser part of exp(-i tau W/(2 hbar)) of both adjacent half steps.
+    int active[3] = {0, 0, 0};
+    if (field)
+        for (int64_t s = 0; s < n; ++s)
+            for (int a = 0; a < nd; ++a)
+                if (field[s * nd + a] != 0.0) active[a] = 1;
+    const bool any_field = active[0] || active[1] || active[2];
+    if (any_field) {
+        if (p->fvec_cap < (n + 1) * nd) {
+            cudaStreamSynchronize(p->stream);
+            dfree(p->fvec);
+            p->fvec = nullptr;
+            p->fvec_cap = 0;
+            rc = dalloc(&p->fvec, (size_t)(n + 1) * nd * sizeof(double), "field vectors");
+            if (rc) return rc;
+            p->fvec_cap = (n + 1) * nd;
+        }
+        std::vector<double> fv((size_t)(n + 1) * nd);
+        const double k = -p->prm.charge * dt / (2.0 * hbar);
+        for (int64_t P = 0; P <= n; ++P)
+            for (int a = 0; a < nd; ++a) fv[P * nd + a] = k * (sample(P - 1, a) + sample(P, a));
+        rc = upload(p, p->fvec, fv.data(), (int64_t)fv.size());
+        if (rc) return rc;
+    }
+    int64_t offs[3] = {0, 0, 0};
+    int64_t row_len = 0;
+    for (int a = 0; a < nd; ++a)
+        if (active[a]) {
+            offs[a] = row_len;
+            row_len += p->dims[a];
+        }
+
+    for (int64_t P0 = 0; P0 <= n; P0 += kFieldChunk) {
+        const int64_t P1 = std::min<int64_t>(n + 1, P0 + kFieldChunk);
+        if (any_field) {
+            Bracket br(p, 4);
+            cudaError_t e = build_field_tables(p->ftab, p->fvec + P0 * nd, P1 - P0, nd, p->dims, p->h, active, offs,
+                                               row_len, p->f64, p->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "build_field_tables");
+            br.done();
+        }
+        auto frow = [&](int64_t P, int a) -> const void * {
+            if (!active[a]) return nullptr;
+            return static_cast<const char *>(p->ftab) + ((P - P0) * row_len + offs[a]) * p->csz;
+        };
+        if (nd == 1) {
+            Args1D a1{};
+            a1.psi = p->psi;
+            a1.n_rows = 1;
+            a1.n_steps = n;
+            a1.p_begin = P0;
+            a1.p_end = P1;
+            a1.p_table0 = P0;
+            a1.tw = p->tw[0];
+            a1.vhalf = p->v_set ? p->vhalf : nullptr;
+            a1.vfull = p->v_set ? p->vfull : nullptr;
+            a1.ftab = any_field ? p->ftab : nullptr;
+            a1.ttab = p->kin[0];
+            a1.scale_hi = p->scale_hi;
+            a1.scale_lo = p->scale_lo;
+            Bracket br(p, 3);
+            cudaError_t e = p->f64 ? launch_1d_f64(a1, (int)p->dims[0], p->stream)
+                                   : launch_1d_f32(a1, (int)p->dims[0], p->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "1D step kernel");
+            br.done();
+            continue;
+        }
+        for (int64_t P = P0; P < P1; ++P) {
+            PassArgs a;
+            base_args(p, a, p->psi, 0);
+            a.pre = P > 0 ? +1 : 0;
+            a.post = P < n ? -1 : 0;
+            a.op = OP_V;
+            a.vtab = p->v_set ? ((P == 0 || P == n) ? p->vhalf : p->vfull) : nullptr;
+            for (int ax = 0; ax < nd; ++ax) a.ftab[ax] = frow(P, ax);
+            rc = run_pass(p, a, 1, 0, "real-space pass");
+            if (rc) return rc;
+            if (P == n) break;
+            if (nd == 2) {
+                PassArgs k;
+                base_args(p, k, p->psi, 1);
+                k.pre = -1;
+                k.post = +1;
+                k.op = OP_T;
+                for (int ax = 0; ax < nd; ++ax) k.ttab[ax] = p->kin[ax];
+                rc = run_pass(p, k, 1, 1, "momentum-space pass");
+                if (rc) return rc;
+            } else {
+                PassArgs y;
+                base_args(p, y, p->psi, 1);
+                y.pre = -1;
+                y.op = OP_NONE;
+                rc = run_pass(p, y, 1, 2, "forward middle-axis pass");
+                if (rc) return rc;
+                PassArgs k;
+                base_args(p, k, p->psi, 2);
+                k.pre = -1;
+                k.post = +1;
+                k.op = OP_T;
+                for (int ax = 0; ax < nd; ++ax) k.ttab[ax] = p->kin[ax];
+                rc = run_pass(p, k, 1, 1, "momentum-space pass");
+                if (rc) return rc;
+                y.pre = +1;
+                rc = run_pass(p, y, 1, 2, "inverse middle-axis pass");
+                if (rc) return rc;
+            }
+        }
+    }
+    return SOP_OK;
+}
+
+int read_result(sop_plan p, int count, double *out) {
+    cudaError_t e = cudaMemcpyAsync(p->host_result, p->result, count * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(result)");
+    e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    for (int i = 0; i < count; ++i) out[i] = p->host_result[i];
+    return SOP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sop_version(void) { return 1; }
+
+const char *sop_last_error(void) { return g_err.c_str(); }
+
+int sop_plan_create(sop_plan *out, int ndim, const int64_t *dims, const double *spacing, int components, int dtype,
+                    const sop_params *params, void *cuda_stream) {
+    if (!out) return fail(SOP_EINVAL, "sop_plan_create: out is NULL");
+    *out = nullptr;
+    if (!dims || !spacing) return fail(SOP_EINVAL, "sop_plan_create: dims or spacing is NULL");
+    if (ndim < 1 || ndim > 3) return fail(SOP_EINVAL, "sop_plan_create: ndim must be 1, 2 or 3");
+    if (dtype != SOP_C64 && dtype != SOP_C128) return fail(SOP_EINVAL, "sop_plan_create: dtype must be SOP_C64 or SOP_C128");
+    if (components != 1 && components != 4) return fail(SOP_EINVAL, "sop_plan_create: components must be 1 or 4");
+    for (int a = 0; a < ndim; ++a) {
+        if (dims[a] <= 0) return fail(SOP_EINVAL, "sop_plan_create: dims must be positive");
+        if (!(spacing[a] > 0) || !is_finite(spacing[a])) return fail(SOP_EINVAL, "sop_plan_create: spacing must be finite and > 0");
+        if (!size_supported(dims[a]))
+            return fail(SOP_EUNSUPPORTED, "sop_plan_create: side " + std::to_string(dims[a]) +
+                                              " is not 2^a*3^b with a>=2, b<=1, 8<=n<=4096");
+    }
+    if (components == 4 && ndim != 2)
+        return fail(SOP_EUNSUPPORTED, "sop_plan_create: the four-component Dirac path supports ndim = 2");
+    sop_params prm{1.0, -1.0, 1.0, 137.036};
+    if (params) prm = *params;
+    if (!(prm.mass > 0) || !(prm.hbar > 0) || !(prm.c > 0) || !is_finite(prm.charge))
+        return fail(SOP_EINVAL, "sop_plan_create: mass, hbar and c must be > 0 and charge finite");
+
+    sop_plan p = new sop_plan_s();
+    p->ndim = ndim;
+    for (int a = 0; a < ndim; ++a) {
+        p->dims[a] = dims[a];
+        p->h[a] = spacing[a];
+    }
+    p->comps = components;
+    p->f64 = dtype == SOP_C128;
+    p->prm = prm;
+    p->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    p->csz = p->f64 ? 16 : 8;
+    p->npts = 1;
+    for (int a = 0; a < ndim; ++a) p->npts *= dims[a];
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        plan_free(p);
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    // 1/N as hi + lo in the working precision.
+    {
+        const double inv = 1.0 / (double)p->npts;
+        if (p->f64) {
+            p->scale_hi = inv;
+            p->scale_lo = 0.0;
+        } else {
+            const float hi = (float)inv;
+            p->scale_hi = hi;
+            p->scale_lo = (double)(float)(inv - (double)hi);
+        }
+    }
+    int rc = SOP_OK;
+    int64_t sum_n = 0;
+    for (int a = 0; a < ndim; ++a) sum_n += dims[a];
+    e = cudaEventCreateWithFlags(&p->stage_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        plan_free(p);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    for (int a = 0; a < ndim && !rc; ++a) {
+        rc = dalloc(&p->tw[a], (size_t)dims[a] * p->csz, "twiddles");
+        if (!rc && components == 1) rc = dalloc(&p->kin[a], (size_t)dims[a] * p->csz, "kinetic table");
+    }
+    if (!rc && components == 4) rc = dalloc(&p->dtab, (size_t)p->npts * 2 * p->csz, "Dirac table");
+    if (!rc) rc = dalloc(&p->theta, (size_t)sum_n * sizeof(double), "angles");
+    if (!rc) rc = dalloc(&p->partial, (size_t)reduce_blocks() * sizeof(double), "partials");
+    if (!rc) rc = dalloc(&p->result, 4 * sizeof(double), "result");
+    if (!rc) rc = dalloc(&p->pgrid, (size_t)sum_n * sizeof(double), "momenta");
+    if (!rc) {
+        p->row_len = sum_n;
+        rc = dalloc(&p->ftab, (size_t)kFieldChunk * sum_n * p->csz, "field tables");
+    }
+    if (!rc) {
+        e = cudaHostAlloc(reinterpret_cast<void **>(&p->host_result), 4 * sizeof(double), cudaHostAllocDefault);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaHostAlloc(result)");
+    }
+    if (rc) {
+        plan_free(p);
+        return rc;
+    }
+    for (int a = 0; a < ndim; ++a) {
+        e = build_twiddles(p->tw[a], (int)dims[a], p->f64, p->stream);
+        if (e != cudaSuccess) {
+            plan_free(p);
+            return cuda_fail(e, "build_twiddles");
+        }
+        p->launches++;
+    }
+    std::vector<double> pg;
+    for (int a = 0; a < ndim; ++a)
+        for (int64_t k = 0; k < dims[a]; ++k) pg.push_back(lattice_p(dims[a], spacing[a], k, prm.hbar));
+    rc = upload(p, p->pgrid, pg.data(), (int64_t)pg.size());
+    if (rc) {
+        plan_free(p);
+        return rc;
+    }
+    e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) {
+        plan_free(p);
+        return cuda_fail(e, "cudaStreamSynchronize(create)");
+    }
+    *out = p;
+    return SOP_OK;
+}
+
+int sop_plan_destroy(sop_plan plan) { return plan_free(plan); }
+
+int sop_bind_state(sop_plan p, void *psi_dev) {
+    if (!p) return fail(SOP_EINVAL, "sop_bind_state: null plan");
+    if (!psi_dev) return fail(SOP_EINVAL, "sop_bind_state: psi is NULL");
+    if (reinterpret_cast<uintptr_t>(psi_dev) % p->csz != 0)
+        return fail(SOP_EINVAL, "sop_bind_state: psi is not aligned to the complex size");
+    p->psi = psi_dev;
+    return SOP_OK;
+}
+
+int sop_set_potential(sop_plan p, const void *V_dev, int v_is_fp64) {
+    if (!p) return fail(SOP_EINVAL, "sop_set_potential: null plan");
+    if (!V_dev) return fail(SOP_EINVAL, "sop_set_potential: V is NULL");
+    if (reinterpret_cast<uintptr_t>(V_dev) % (v_is_fp64 ? 8 : 4) != 0)
+        return fail(SOP_EINVAL, "sop_set_potential: V is misaligned");
+    int rc = SOP_OK;
+    if (!p->V) rc = dalloc(&p->V, (size_t)p->npts * sizeof(double), "potential");
+    if (!rc && !p->vhalf) rc = dalloc(&p->vhalf, (size_t)p->npts * p->csz, "half phase table");
+    if (!rc && !p->vfull) rc = dalloc(&p->vfull, (size_t)p->npts * p->csz, "full phase table");
+    if (rc) return rc;
+    Bracket br(p, 4);
+    cudaError_t e = convert_potential(p->V, V_dev, p->npts, v_is_fp64 != 0, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "convert_potential");
+    br.done();
+    p->v_set = true;
+    p->tables_valid = false;
+    return SOP_OK;
+}
+
+int sop_step(sop_plan p, int64_t n_steps, double dt, const double *field_samples) {
+    return step_impl(p, n_steps, dt, field_samples);
+}
+
+int sop_step_host(sop_plan p, void *psi_host, int64_t n_steps, double dt, const double *field_samples) {
+    if (!p) return fail(SOP_EINVAL, "sop_step_host: null plan");
+    if (!psi_host) return fail(SOP_EINVAL, "sop_step_host: psi_host is NULL");
+    if (!p->psi) return fail(SOP_ESTATE, "sop_step_host: no device state bound");
+    const size_t bytes = (size_t)p->npts * p->comps * p->csz;
+    cudaError_t e = cudaMemcpyAsync(p->psi, psi_host, bytes, cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(H2D)");
+    int rc = step_impl(p, n_steps, dt, field_samples);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(psi_host, p->psi, bytes, cudaMemcpyDeviceToHost, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(D2H)");
+    e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return SOP_OK;
+}
+
+int sop_norm(sop_plan p, double *out) {
+    if (!p || !out) return fail(SOP_EINVAL, "sop_norm: null argument");
+    if (!p->psi) return fail(SOP_ESTATE, "sop_norm: no state bound");
+    double dV = 1.0;
+    for (int a = 0; a < p->ndim; ++a) dV *= p->h[a];
+    Bracket br(p, 4);
+    cudaError_t e = reduce_norm(p->psi, p->npts * p->comps, p->f64, p->partial, p->result, dV, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce_norm");
+    br.done(2);
+    return read_result(p, 1, out);
+}
+
+int sop_energy(sop_plan p, double *out) {
+    if (!p || !out) return fail(SOP_EINVAL, "sop_energy: null argument");
+    if (!p->psi) return fail(SOP_ESTATE, "sop_energy: no state bound");
+    const size_t bytes = (size_t)p->npts * p->comps * p->csz;
+    int rc = SOP_OK;
+    if (!p->scratch) rc = dalloc(&p->scratch, bytes, "energy scratch");
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(p->scratch, p->psi, bytes, cudaMemcpyDeviceToDevice, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(D2D)");
+    for (int ax = 0; ax < p->ndim; ++ax) {
+        PassArgs a;
+        base_args(p, a, p->scratch, ax);
+        a.n_batch = p->comps;
+        a.pre = -1;
+        a.op = OP_NONE;
+        rc = run_pass(p, a, 1, 2, "energy forward transform");
+        if (rc) return rc;
+    }
+    double dV = 1.0;
+    for (int a = 0; a < p->ndim; ++a) dV *= p->h[a];
+    Bracket br(p, 4);
+    e = reduce_energy_t(p->scratch, p->ndim, p->dims, p->pgrid, p->comps, p->prm.mass, p->prm.c, p->f64, p->partial,
+                        p->result, dV / (double)p->npts, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce_energy_t");
+    int nl = 2;
+    if (p->v_set) {
+        e = reduce_energy_v(p->psi, p->V, p->npts, p->comps, p->f64, p->partial, p->result + 1, dV, p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "reduce_energy_v");
+        nl += 2;
+    } else {
+        cudaMemsetAsync(p->result + 1, 0, sizeof(double), p->stream);
+    }
+    br.done(nl);
+    double r[2];
+    rc = read_result(p, 2, r);
+    if (rc) return rc;
+    *out = r[0] + r[1];
+    return SOP_OK;
+}
+
+int sop_profile_enable(sop_plan p, int on) {
+    if (!p) return fail(SOP_EINVAL, "sop_profile_enable: null plan");
+    p->prof = on != 0;
+    return SOP_OK;
+}
+
+int sop_profile_read(sop_plan p, double *ms, int64_t *launches, int max_classes) {
+    if (!p || !ms || !launches || max_classes <= 0) return fail(SOP_EINVAL, "sop_profile_read: bad argument");
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    for (int c = 0; c < max_classes; ++c) {
+        ms[c] = 0.0;
+        launches[c] = 0;
+    }
+    for (auto &ep : p->events) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ep.a, ep.b);
+        if (ep.cls < max_classes) {
+            ms[ep.cls] += t;
+            launches[ep.cls] += 1;
+        }
+        p->event_pool.push_back(ep.a);
+        p->event_pool.push_back(ep.b);
+    }
+    p->events.clear();
+    return SOP_OK;
+}
+
+int64_t sop_launch_counter(sop_plan p) { return p ? p->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,291 @@
+// sop_fft.cuh -- in-register / shared-memory Stockham FFT engine for sm_103a.
+//
+// Sec. 2.1 of Bauke & Keitel (arXiv:1012.3911): on a lattice of N points the
+// Fourier transforms of the split step become DFTs, X_k = sum_j x_j
+// exp(-2 pi i jk/n) per axis, computed here by mixed-radix FFTs.
+//
+// Design (one pencil of n points, one CTA-resident exchange buffer):
+//  * T = n/E threads per pencil, each holding E complex values in registers.
+//    Thread t always holds the elements t + T*m, m = 0..E-1, of the current
+//    stage's input ("natural mapping"); global loads/stores in this mapping
+//    are coalesced along t.
+//  * Stage s (radix R, Ns = product of the earlier radices) is the Stockham
+//    autosort step: butterfly j (j < n/R) reads x[j + r n/R], multiplies
+//    input r by W_{Ns R}^{(j mod Ns) r}, does an R-point DFT in registers and
+//    writes output r to y[(j div Ns) Ns R + (j mod Ns) + r Ns].  With
+//    j = t + T q the inputs of thread t are exactly its registers
+//    q + r (E/R), so only the outputs go through shared memory; the last
+//    stage's outputs land back in the natural mapping without an exchange.
+//  * The inverse transform is conj(F(conj(x))): only the forward code is
+//    compiled.
+//  * Stage twiddles come from a per-size table W_n^e, e < n, formed in FP64
+//    on the device and rounded once to the working precision; the constant
+//    twiddles inside the radix-4/8/16 butterflies are the exact decimal
+//    expansions of cos/sin(k pi/8) rounded by the compiler.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sop {
+
+template <typename R> struct CplxOf;
+template <> struct CplxOf<float> { using type = float2; };
+template <> struct CplxOf<double> { using type = double2; };
+template <typename R> using cplx_t = typename CplxOf<R>::type;
+
+__device__ __forceinline__ float fmar(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmar(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename C> __device__ __forceinline__ C mk(decltype(C::x) re, decltype(C::x) im) {
+    C r;
+    r.x = re;
+    r.y = im;
+    return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    return mk<C>(fmar(a.x, b.x, -(a.y * b.y)), fmar(a.x, b.y, a.y * b.x));
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return mk<C>(a.x, -a.y); }
+template <typename C> __device__ __forceinline__ C mul_mi(C a) { return mk<C>(a.y, -a.x); }  // a * (-i)
+template <typename C> __device__ __forceinline__ C mul_pi(C a) { return mk<C>(-a.y, a.x); }  // a * (+i)
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return mk<C>(a.x * s, a.y * s); }
+
+// a * exp(-2 pi i J / 16), 0 <= J < 8 (the only angles the radix-2^k
+// butterflies below need).
+template <int J, typename C> __device__ __forceinline__ C w16(C a) {
+    using R = decltype(a.x);
+    constexpr R c1 = R(0.92387953251128675612818318939678828682);  // cos(pi/8)
+    constexpr R s1 = R(0.38268343236508977172845998403039886676);  // sin(pi/8)
+    constexpr R r2 = R(0.70710678118654752440084436210484903928);  // cos(pi/4)
+    if constexpr (J == 0) return a;
+    else if constexpr (J == 4) return mul_mi(a);
+    else if constexpr (J == 2) return mk<C>((a.x + a.y) * r2, (a.y - a.x) * r2);
+    else if constexpr (J == 6) return mk<C>((a.y - a.x) * r2, -(a.x + a.y) * r2);
+    else if constexpr (J == 1) return mk<C>(fmar(a.x, c1, a.y * s1), fmar(a.y, c1, -(a.x * s1)));
+    else if constexpr (J == 3) return mk<C>(fmar(a.x, s1, a.y * c1), fmar(a.y, s1, -(a.x * c1)));
+    else if constexpr (J == 5) return mk<C>(fmar(a.y, c1, -(a.x * s1)), -fmar(a.y, s1, a.x * c1));
+    else return mk<C>(fmar(a.y, s1, -(a.x * c1)), -fmar(a.y, c1, a.x * s1));   // J == 7
+}
+
+template <int R> struct Dft;
+
+template <int R, int K, typename C> __device__ __forceinline__ void dit_combine(C *x, const C *e, const C *o) {
+    if constexpr (K < R / 2) {
+        const C t = w16<K * 16 / R>(o[K]);
+        x[K] = cadd(e[K], t);
+        x[K + R / 2] = csub(e[K], t);
+        dit_combine<R, K + 1>(x, e, o);
+    }
+}
+
+// Forward R-point DFT in registers, natural order in and out.
+template <int R> struct Dft {
+    template <typename C> __device__ __forceinline__ static void run(C *x) {
+        if constexpr (R == 1) {
+        } else if constexpr (R == 2) {
+            const C a = x[0], b = x[1];
+            x[0] = cadd(a, b);
+            x[1] = csub(a, b);
+        } else if constexpr (R == 3) {
+            using T = decltype(x[0].x);
+            constexpr T h = T(0.5);
+            constexpr T r3 = T(0.86602540378443864676372317075293618347);  // sin(pi/3)
+            const C a = x[0];
+            const C s = cadd(x[1], x[2]);
+            const C d = csub(x[1], x[2]);
+            x[0] = cadd(a, s);
+            const C m = mk<C>(fmar(-h, s.x, a.x), fmar(-h, s.y, a.y));
+            const C u = cscale(d, r3);
+            x[1] = mk<C>(m.x + u.y, m.y - u.x);  // m - i u
+            x[2] = mk<C>(m.x - u.y, m.y + u.x);  // m + i u
+        } else {
+            static_assert(R == 4 || R == 8 || R == 16, "radix");
+            constexpr int H = R / 2;
+            C e[H], o[H];
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                e[k] = x[2 * k];
+                o[k] = x[2 * k + 1];
+            }
+            Dft<H>::run(e);
+            Dft<H>::run(o);
+            dit_combine<R, 0>(x, e, o);
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Compile-time stage plan
+// ---------------------------------------------------------------------------
+
+struct StagePlan {
+    int S;       // number of stages
+    int R[8];    // radix of each stage
+    int NS[8];   // product of the radices before each stage
+};
+
+__host__ __device__ constexpr int pow2_part(int x) {
+    int p = 1;
+    while (x % 2 == 0) {
+        x /= 2;
+        p *= 2;
+    }
+    return p;
+}
+
+// Radices: the largest power of two dividing E while it fits, then the
+// power-of-two remainder, then one radix-3 stage if 3 | n.
+__host__ __device__ constexpr StagePlan make_plan(int n, int E) {
+    StagePlan p{0, {0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0, 0, 0}};
+    const bool has3 = (n % 3) == 0;
+    int rem = has3 ? n / 3 : n;
+    const int rmax = pow2_part(E);
+    while (rem >= rmax && rem > 1) {
+        p.R[p.S++] = rmax;
+        rem /= rmax;
+    }
+    if (rem > 1) p.R[p.S++] = rem;
+    if (has3) p.R[p.S++] = 3;
+    int ns = 1;
+    for (int s = 0; s < p.S; ++s) {
+        p.NS[s] = ns;
+        ns *= p.R[s];
+    }
+    return p;
+}
+
+__host__ __device__ constexpr int ilog2c(int x) {
+    int r = 0;
+    while ((1 << r) < x) ++r;
+    return r;
+}
+
+// Elements per thread: 16 (scalar) or 8 (two coupled components) for powers
+// of two; for n = 3*2^k, 8*3 or 4*3.  Small sizes use one thread per pencil.
+template <int N, int NC> struct Geometry {
+    static constexpr int E_calc() {
+        if (N % 3 == 0) {
+            int base = (NC == 1) ? 8 : 4;
+            const int p2 = N / 3;
+            if (p2 < base) base = p2;
+            return base * 3;
+        }
+        const int e = (NC == 1) ? 16 : 8;
+        return N < e ? N : e;
+    }
+    static constexpr int E = E_calc();
+    static constexpr int T = N / E;
+    static constexpr StagePlan P = make_plan(N, E);
+    static constexpr int LR = ilog2c(P.R[0] == 3 ? 2 : P.R[0]);   // log2 of the first radix
+    static_assert(N % E == 0, "E must divide N");
+};
+
+// ---------------------------------------------------------------------------
+// Shared-memory exchange layouts
+// ---------------------------------------------------------------------------
+
+// One pencil stored contiguously with one pad element per 2^LR elements, so
+// the stride-R writes of the first stage and the unit-stride reads both map
+// consecutive threads to distinct banks.
+template <typename C, int LR> struct LayContig {
+    C *p;
+    __device__ __forceinline__ static int off(int i) { return i + (i >> LR); }
+    __device__ __forceinline__ void st(int i, C v) const { p[off(i)] = v; }
+    __device__ __forceinline__ C ld(int i) const { return p[off(i)]; }
+};
+
+// WP pencils interleaved as rows [i][w] (w fastest, matching the coalesced
+// global layout of a strided axis).  When a row is shorter than 128 bytes,
+// LM+1 rows share a bank line; the row index is XOR-swizzled so the
+// stride-R first-stage writes of the warp spread over the line.
+template <typename C, int WP, int SH, int LM> struct LayStrided {
+    C *p;  // tile base + pencil column
+    __device__ __forceinline__ static int off(int i) { return (i ^ ((i >> SH) & LM)) * WP; }
+    __device__ __forceinline__ void st(int i, C v) const { p[off(i)] = v; }
+    __device__ __forceinline__ C ld(int i) const { return p[off(i)]; }
+};
+
+template <typename C> __device__ __forceinline__ C ldg_c(const C *p) { return __ldg(p); }
+
+// One Stockham stage (see the header comment).  tw: W_n^e table.
+template <typename C, int N, int E, int S, typename Lay>
+__device__ __forceinline__ void fft_stage(C (&v)[E], const Lay &lay, int t, const C *__restrict__ tw) {
+    constexpr StagePlan P = make_plan(N, E);
+    constexpr int R = P.R[S];
+    constexpr int NS = P.NS[S];
+    constexpr int T = N / E;
+    constexpr int Q = E / R;
+    constexpr bool LAST = (S == P.S - 1);
+    static_assert(E % R == 0, "radix must divide E");
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int j = t + T * q;
+        const int k = j % NS;
+        C x[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r] = v[q + r * Q];
+        if constexpr (NS > 1) {
+            constexpr int STEP = N / (NS * R);
+#pragma unroll
+            for (int r = 1; r < R; ++r) x[r] = cmul(x[r], ldg_c(tw + k * r * STEP));
+        }
+        Dft<R>::run(x);
+        if constexpr (LAST) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[q + r * Q] = x[r];
+        } else {
+            const int ob = (j / NS) * NS * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) lay.st(ob + r * NS, x[r]);
+        }
+    }
+}
+
+// Forward FFT of NC pencils held by this thread group, natural mapping in
+// and out.  Every thread of the CTA must call it (it contains barriers).
+template <typename C, int N, int E, int NC, int S, typename Lay>
+__device__ __forceinline__ void fft_forward_from(C (&v)[NC][E], const Lay (&lay)[NC], int t,
+                                                 const C *__restrict__ tw) {
+    constexpr StagePlan P = make_plan(N, E);
+    if constexpr (S < P.S) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) fft_stage<C, N, E, S>(v[c], lay[c], t, tw);
+        if constexpr (S + 1 < P.S) {
+            constexpr int T = N / E;
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int m = 0; m < E; ++m) v[c][m] = lay[c].ld(t + T * m);
+            __syncthreads();
+        }
+        fft_forward_from<C, N, E, NC, S + 1>(v, lay, t, tw);
+    }
+}
+
+template <typename C, int N, int E, int NC, typename Lay>
+__device__ __forceinline__ void fft_forward(C (&v)[NC][E], const Lay (&lay)[NC], int t,
+                                            const C *__restrict__ tw) {
+    fft_forward_from<C, N, E, NC, 0>(v, lay, t, tw);
+}
+
+template <typename C, int E, int NC> __device__ __forceinline__ void conj_all(C (&v)[NC][E]) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[c][m].y = -v[c][m].y;
+}
+
+// dir < 0: forward DFT; dir > 0: inverse DFT without the 1/n factor.
+template <typename C, int N, int E, int NC, typename Lay>
+__device__ __forceinline__ void fft_dir(C (&v)[NC][E], const Lay (&lay)[NC], int t,
+                                        const C *__restrict__ tw, int dir) {
+    if (dir > 0) conj_all<C, E, NC>(v);
+    fft_forward<C, N, E, NC>(v, lay, t, tw);
+    if (dir > 0) conj_all<C, E, NC>(v);
+}
+
+}  // namespace sop

@@ -1,0 +1,106 @@
+// sop_internal.h -- declarations shared by the host driver and the kernel
+// translation units of libsop.so (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sop {
+
+// Pointwise operator applied between the two transforms of a pass.
+enum PassOp : int {
+    OP_NONE = 0,  // transforms only
+    OP_V = 1,     // Schroedinger real-space factor (Eq. 11, length-gauge field)
+    OP_T = 2,     // Schroedinger momentum-space factor (Eq. 13) and 1/N
+    OP_DV = 3,    // Dirac real-space factor (Eqs. 21-26), one component pair
+    OP_DT = 4,    // Dirac momentum-space factor (Eq. 33 in closed form) and 1/N
+};
+
+// Arguments of one pencil pass along one axis.  A "pencil" is the set of
+// n = dims[axis] points that differ only in the axis index.
+struct PassArgs {
+    void *psi;               // complex array of the plan's dtype
+    int64_t comp_stride;     // points per component (prod dims)
+    int64_t n_pencils;       // pencils per batch entry (prod of the other dims)
+    int n_batch;             // independent copies (components treated as a batch)
+    int64_t stride;          // element stride along the axis = prod(dims[0..axis-1])
+    int ndim;
+    int axis;
+    int64_t dims[3];
+    int pre;                 // transform before the operator: 0 none, -1 forward, +1 inverse
+    int post;                // transform after the operator
+    int op;                  // PassOp
+    const void *tw;          // twiddles exp(-2 pi i e / n), e < n, plan dtype
+    // OP_V / OP_DV: per-point phase table (z-form for FP32, factor for FP64), may be null
+    const void *vtab;
+    // OP_V: per-axis field phase tables of this pass (null = axis has no field)
+    const void *ftab[3];
+    // OP_T: per-axis kinetic tables
+    const void *ttab[3];
+    // OP_DT: per-momentum table (cos, sin*mc^2/E, sin*c p_x/E, sin*c p_y/E)
+    const void *dtab;
+    double scale_hi, scale_lo;   // 1/N as an unevaluated sum hi + lo
+    // OP_DV: 2x2 complex block per component pair (re, im of m00, m01, m10, m11)
+    double mix[2][8];
+    int pair_comp[2][2];     // component indices of each pair
+};
+
+// Arguments of the one-dimensional whole-step kernel.
+struct Args1D {
+    void *psi;
+    int64_t n_rows;          // independent 1D problems
+    int64_t n_steps;         // steps of the whole sop_step call
+    int64_t p_begin, p_end;  // real-space factor indices handled by this launch
+    int64_t p_table0;        // index of the first field-table row in ftab
+    const void *tw;
+    const void *vhalf, *vfull;   // phase tables (may be null)
+    const void *ftab;            // field tables, row per real-space index, n entries (may be null)
+    const void *ttab;            // kinetic table
+    double scale_hi, scale_lo;
+};
+
+// Launchers, one translation unit per dtype and axis kind (sop_pass_inst.cu
+// compiled four times, sop_1d_inst.cu twice).  nc: coupled components per
+// pencil (1 or 2).  They return cudaErrorInvalidValue for a size without a
+// kernel.
+cudaError_t launch_pass_f32_contig(const PassArgs &a, int nc, cudaStream_t s);
+cudaError_t launch_pass_f32_strided(const PassArgs &a, int nc, cudaStream_t s);
+cudaError_t launch_pass_f64_contig(const PassArgs &a, int nc, cudaStream_t s);
+cudaError_t launch_pass_f64_strided(const PassArgs &a, int nc, cudaStream_t s);
+cudaError_t launch_1d_f32(const Args1D &a, int n, cudaStream_t s);
+cudaError_t launch_1d_f64(const Args1D &a, int n, cudaStream_t s);
+// Threads and dynamic shared memory of the pass kernel for (dtype, n, nc, contig).
+bool pass_geometry(bool f64, int n, int nc, bool contig, int *threads, int *pencils_per_cta, int *smem);
+
+// Sides with a kernel: 2^a * 3^b, a >= 2, b <= 1, 8 <= n <= 4096.
+inline bool size_supported(int64_t n) {
+    if (n < 8 || n > 4096) return false;
+    if (n % 3 == 0) n /= 3;
+    if (n < 4) return false;
+    return (n & (n - 1)) == 0;
+}
+
+// Table set-up kernels (sop_tables.cu).  All phases are formed in FP64.
+cudaError_t build_twiddles(void *out, int n, bool f64, cudaStream_t s);
+cudaError_t build_vphase(void *out, const double *V, int64_t npts, double factor, bool f64,
+                         cudaStream_t s);
+cudaError_t build_axis_phase(void *out, const double *coef, int n, bool f64, cudaStream_t s);
+cudaError_t build_field_tables(void *out, const double *fvec, int64_t n_rows, int ndim,
+                               const int64_t *dims, const double *spacing, const int *active,
+                               const int64_t *offsets, int64_t row_len, bool f64, cudaStream_t s);
+cudaError_t build_dirac_table(void *out, const int64_t *dims, const double *spacing, double mass,
+                              double c, double hbar, double dt, bool f64, cudaStream_t s);
+cudaError_t convert_potential(double *out, const void *in, int64_t n, bool in_f64, cudaStream_t s);
+
+// Reductions (sop_reduce.cu).  partial must hold reduce_blocks() doubles.
+int reduce_blocks();
+cudaError_t reduce_norm(const void *psi, int64_t n, bool f64, double *partial, double *out,
+                        double scale, cudaStream_t s);
+cudaError_t reduce_energy_v(const void *psi, const double *V, int64_t npts, int comps, bool f64,
+                            double *partial, double *out, double scale, cudaStream_t s);
+cudaError_t reduce_energy_t(const void *psit, int ndim, const int64_t *dims,
+                            const double *pgrid /* concatenated per-axis momenta */, int comps,
+                            double mass, double c, bool f64, double *partial, double *out,
+                            double scale, cudaStream_t s);
+
+}  // namespace sop

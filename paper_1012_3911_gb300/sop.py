@@ -1,0 +1,262 @@
+"""Thin ctypes binding of libsop.so (the ``sop_*`` C ABI of ``include/sop.h``).
+
+Functions carry the C names and only marshal arguments: every step of the
+split-operator path runs in the library's CUDA kernels.  PyTorch provides the
+device memory and the stream.  The library must have been built
+(``paper_1012_3911_gb300.build.build()``); there is no fallback, and a missing
+library raises ``RuntimeError``.
+
+Shapes: ``dims`` is given in axis order (n_x, n_y, n_z) as in the C ABI; a
+state tensor has the NumPy/PyTorch shape (C, n_z, n_y, n_x) with the leading
+component axis only for Dirac (C = 4).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsop.so")
+
+SOP_C64, SOP_C128 = 0, 1
+SOP_OK, SOP_EINVAL, SOP_EUNSUPPORTED, SOP_ENOMEM, SOP_ECUDA, SOP_ETIMEOUT, SOP_ESTATE = 0, -1, -2, -3, -4, -5, -6
+SOP_PASS_CLASSES = 5
+PASS_CLASS_NAMES = ("real_space_pass", "momentum_space_pass", "middle_axis_pass", "whole_step_1d", "table_setup")
+
+_lib = None
+_lock = threading.Lock()
+
+
+class SopError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"sop status {status}: {message}")
+        self.status = status
+
+
+class sop_params(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("charge", ctypes.c_double), ("hbar", ctypes.c_double),
+                ("c", ctypes.c_double)]
+
+
+def load(path: str = LIB_PATH):
+    """Load libsop.so (once).  Raises RuntimeError if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_1012_3911_gb300.build.build(); "
+                               "the split-operator path has no CPU fallback")
+        lib = ctypes.CDLL(path)
+        vp, i64, d, i = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+        lib.sop_plan_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(i64), ctypes.POINTER(d), i, i,
+                                        ctypes.POINTER(sop_params), vp]
+        lib.sop_plan_destroy.argtypes = [vp]
+        lib.sop_bind_state.argtypes = [vp, vp]
+        lib.sop_set_potential.argtypes = [vp, vp, i]
+        lib.sop_step.argtypes = [vp, i64, d, vp]
+        lib.sop_step_host.argtypes = [vp, vp, i64, d, vp]
+        lib.sop_norm.argtypes = [vp, ctypes.POINTER(d)]
+        lib.sop_energy.argtypes = [vp, ctypes.POINTER(d)]
+        lib.sop_profile_enable.argtypes = [vp, i]
+        lib.sop_profile_read.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i64), i]
+        lib.sop_launch_counter.argtypes = [vp]
+        lib.sop_launch_counter.restype = i64
+        lib.sop_last_error.restype = ctypes.c_char_p
+        lib.sop_version.restype = i
+        for name in ("sop_plan_create", "sop_plan_destroy", "sop_bind_state", "sop_set_potential", "sop_step",
+                     "sop_step_host", "sop_norm", "sop_energy", "sop_profile_enable", "sop_profile_read"):
+            getattr(lib, name).restype = i
+        _lib = lib
+        return lib
+
+
+def sop_last_error() -> str:
+    return load().sop_last_error().decode()
+
+
+def sop_version() -> int:
+    return int(load().sop_version())
+
+
+def _check(rc: int) -> None:
+    if rc != SOP_OK:
+        raise SopError(rc, sop_last_error())
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def sop_plan_create(dims: Sequence[int], spacing: Sequence[float], components: int = 1, dtype: int = SOP_C64,
+                    params: Optional[dict] = None, stream=None) -> int:
+    """Create a plan; returns the opaque handle (an int).  ``stream`` is a
+    torch.cuda.Stream, a raw handle, or None for torch's current stream."""
+    lib = load()
+    nd = len(dims)
+    cd = (ctypes.c_int64 * nd)(*[int(x) for x in dims])
+    cs = (ctypes.c_double * nd)(*[float(x) for x in spacing])
+    pp = None
+    if params is not None:
+        pr = sop_params(params.get("mass", 1.0), params.get("charge", -1.0), params.get("hbar", 1.0),
+                        params.get("c", 137.036))
+        pp = ctypes.pointer(pr)
+    out = ctypes.c_void_p()
+    _check(lib.sop_plan_create(ctypes.byref(out), nd, cd, cs, int(components), int(dtype), pp,
+                               _stream_handle(stream)))
+    return out.value
+
+
+def sop_plan_destroy(plan: int) -> None:
+    _check(load().sop_plan_destroy(plan))
+
+
+def sop_bind_state(plan: int, psi) -> None:
+    """Bind a contiguous CUDA tensor (complex64/complex128) as the state."""
+    if not psi.is_cuda or not psi.is_contiguous():
+        raise ValueError("psi must be a contiguous CUDA tensor")
+    _check(load().sop_bind_state(plan, psi.data_ptr()))
+
+
+def sop_set_potential(plan: int, V) -> None:
+    """Copy a CUDA float32/float64 tensor of prod(dims) values as V."""
+    import torch
+    if not V.is_cuda or not V.is_contiguous():
+        raise ValueError("V must be a contiguous CUDA tensor")
+    if V.dtype not in (torch.float32, torch.float64):
+        raise ValueError("V must be float32 or float64")
+    _check(load().sop_set_potential(plan, V.data_ptr(), int(V.dtype == torch.float64)))
+
+
+def _field_ptr(field, n_steps: int, ndim: int):
+    if field is None:
+        return None, None
+    f = np.ascontiguousarray(np.asarray(field, dtype=np.float64).reshape(int(n_steps), ndim))
+    return f, f.ctypes.data
+
+
+def sop_step(plan: int, n_steps: int, dt: float, field=None, ndim: Optional[int] = None) -> None:
+    """Asynchronous: n_steps Strang steps of size dt on the bound state.
+    ``field`` (host) has n_steps rows of ndim samples, or None."""
+    keep, ptr = (None, None)
+    if field is not None:
+        nd = ndim if ndim is not None else np.asarray(field).reshape(int(n_steps), -1).shape[1]
+        keep, ptr = _field_ptr(field, n_steps, nd)
+    _check(load().sop_step(plan, int(n_steps), float(dt), ptr))
+    del keep
+
+
+def sop_step_host(plan: int, psi_host, n_steps: int, dt: float, field=None, ndim: Optional[int] = None) -> None:
+    """Copy a host tensor/array in, step, copy it back (synchronous)."""
+    if hasattr(psi_host, "data_ptr"):
+        if psi_host.is_cuda or not psi_host.is_contiguous():
+            raise ValueError("psi_host must be a contiguous CPU tensor")
+        hptr = psi_host.data_ptr()
+    else:
+        if not psi_host.flags["C_CONTIGUOUS"]:
+            raise ValueError("psi_host must be C-contiguous")
+        hptr = psi_host.ctypes.data
+    keep, ptr = (None, None)
+    if field is not None:
+        nd = ndim if ndim is not None else np.asarray(field).reshape(int(n_steps), -1).shape[1]
+        keep, ptr = _field_ptr(field, n_steps, nd)
+    _check(load().sop_step_host(plan, hptr, int(n_steps), float(dt), ptr))
+    del keep
+
+
+def sop_norm(plan: int) -> float:
+    out = ctypes.c_double()
+    _check(load().sop_norm(plan, ctypes.byref(out)))
+    return out.value
+
+
+def sop_energy(plan: int) -> float:
+    out = ctypes.c_double()
+    _check(load().sop_energy(plan, ctypes.byref(out)))
+    return out.value
+
+
+def sop_profile_enable(plan: int, on: bool = True) -> None:
+    _check(load().sop_profile_enable(plan, int(bool(on))))
+
+
+def sop_profile_read(plan: int):
+    """Returns (ms per pass class, launches per pass class) and resets them."""
+    ms = (ctypes.c_double * SOP_PASS_CLASSES)()
+    n = (ctypes.c_int64 * SOP_PASS_CLASSES)()
+    _check(load().sop_profile_read(plan, ms, n, SOP_PASS_CLASSES))
+    return list(ms), list(n)
+
+
+def sop_launch_counter(plan: int) -> int:
+    return int(load().sop_launch_counter(plan))
+
+
+class Propagator:
+    """A plan plus its bound torch state.
+
+    >>> prop = Propagator(dims=(2048, 2048), spacing=(h, h), dtype="c64")
+    >>> prop.state.copy_(psi0); prop.set_potential(V)
+    >>> prop.step(5000, 0.02, field)        # asynchronous
+    >>> prop.norm(), prop.energy()
+    """
+
+    def __init__(self, dims: Sequence[int], spacing: Sequence[float], components: int = 1,
+                 dtype: str = "c64", params: Optional[dict] = None, stream=None, device=None):
+        import torch
+        self.dims = tuple(int(x) for x in dims)
+        self.ndim = len(self.dims)
+        self.components = int(components)
+        self.dtype = dtype
+        tdt = {"c64": torch.complex64, "c128": torch.complex128}[dtype]
+        shape = self.dims[::-1]
+        if self.components > 1:
+            shape = (self.components,) + shape
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.state = torch.zeros(shape, dtype=tdt, device=dev)
+        self.plan = sop_plan_create(self.dims, spacing, components, SOP_C64 if dtype == "c64" else SOP_C128,
+                                    params, stream)
+        sop_bind_state(self.plan, self.state)
+
+    def set_state(self, psi) -> None:
+        import torch
+        self.state.copy_(torch.as_tensor(psi).to(self.state.dtype))
+
+    def set_potential(self, V) -> None:
+        import torch
+        Vt = torch.as_tensor(np.ascontiguousarray(V) if isinstance(V, np.ndarray) else V)
+        if Vt.dtype not in (torch.float32, torch.float64):
+            Vt = Vt.double()
+        sop_set_potential(self.plan, Vt.to(self.state.device).contiguous())
+
+    def step(self, n_steps: int, dt: float, field=None) -> None:
+        sop_step(self.plan, n_steps, dt, field, self.ndim)
+
+    def step_host(self, psi_host, n_steps: int, dt: float, field=None) -> None:
+        sop_step_host(self.plan, psi_host, n_steps, dt, field, self.ndim)
+
+    def norm(self) -> float:
+        return sop_norm(self.plan)
+
+    def energy(self) -> float:
+        return sop_energy(self.plan)
+
+    def close(self) -> None:
+        if getattr(self, "plan", None):
+            sop_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
