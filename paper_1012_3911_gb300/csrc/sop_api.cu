@@ -568,7 +568,7 @@ int sop_plan_create(sop_plan *out, int ndim, const int64_t *dims, const double *
         return cuda_fail(e, "cudaEventCreate");
     }
     for (int a = 0; a < ndim && !rc; ++a) {
-        rc = dalloc(&p->tw[a], (size_t)dims[a] * p->csz, "twiddles");
+        rc = dalloc(&p->tw[a], (size_t)dims[a] * 16, "twiddles");   // float4 hi/lo or double2
         if (!rc && components == 1) rc = dalloc(&p->kin[a], (size_t)dims[a] * p->csz, "kinetic table");
     }
     if (!rc && components == 4) rc = dalloc(&p->dtab, (size_t)p->npts * 2 * p->csz, "Dirac table");

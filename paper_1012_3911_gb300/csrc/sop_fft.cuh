@@ -19,9 +19,10 @@
 //  * The inverse transform is conj(F(conj(x))): only the forward code is
 //    compiled.
 //  * Stage twiddles come from a per-size table W_n^e, e < n, formed in FP64
-//    on the device and rounded once to the working precision; the constant
-//    twiddles inside the radix-4/8/16 butterflies are the exact decimal
-//    expansions of cos/sin(k pi/8) rounded by the compiler.
+//    on the device; the FP32 table keeps each value as an unevaluated sum
+//    hi + lo, and the constants inside the radix-3/4/8/16 butterflies are
+//    applied the same way (see kmul below), so no rounded constant biases
+//    the modulus of a transform.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -53,22 +54,58 @@ template <typename C> __device__ __forceinline__ C mul_mi(C a) { return mk<C>(a.
 template <typename C> __device__ __forceinline__ C mul_pi(C a) { return mk<C>(-a.y, a.x); }  // a * (+i)
 template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return mk<C>(a.x * s, a.y * s); }
 
+// Butterfly constants.  In FP32 every non-trivial constant is applied as an
+// unevaluated sum hi + lo (x*c = fma(x, hi, x*lo)): a rounded constant alone
+// would give each twiddle a modulus |w| != 1 with a fixed sign, and a
+// decimation-in-time combine e +- w o changes the norm by 2(|w|^2 - 1)|o|^2,
+// which then recurs identically in every transform of every step.  With the
+// pair the constant is exact to ~2^-48 and only the unbiased rounding of the
+// data remains.  FP64 uses the constants directly.
+enum KId { K_C1 = 0, K_S1 = 1, K_R2 = 2, K_R3 = 3 };
+template <int ID> struct KVal;
+template <> struct KVal<K_C1> { static constexpr double v = 0.92387953251128675612818318939678828682; };  // cos(pi/8)
+template <> struct KVal<K_S1> { static constexpr double v = 0.38268343236508977172845998403039886676; };  // sin(pi/8)
+template <> struct KVal<K_R2> { static constexpr double v = 0.70710678118654752440084436210484903928; };  // cos(pi/4)
+template <> struct KVal<K_R3> { static constexpr double v = 0.86602540378443864676372317075293618347; };  // sin(pi/3)
+
+template <int ID> __device__ __forceinline__ float kmul(float x) {
+    constexpr float hi = (float)KVal<ID>::v;
+    constexpr float lo = (float)(KVal<ID>::v - (double)hi);
+    return fmar(x, hi, x * lo);
+}
+template <int ID> __device__ __forceinline__ double kmul(double x) { return x * KVal<ID>::v; }
+
+// a*c_A + b*c_B
+template <int A, int B> __device__ __forceinline__ float kdot(float a, float b) {
+    constexpr float ah = (float)KVal<A>::v, al = (float)(KVal<A>::v - (double)ah);
+    constexpr float bh = (float)KVal<B>::v, bl = (float)(KVal<B>::v - (double)bh);
+    return fmar(a, ah, fmar(b, bh, fmar(a, al, b * bl)));
+}
+template <int A, int B> __device__ __forceinline__ double kdot(double a, double b) {
+    return fmar(a, KVal<A>::v, b * KVal<B>::v);
+}
+
 // a * exp(-2 pi i J / 16), 0 <= J < 8 (the only angles the radix-2^k
 // butterflies below need).
 template <int J, typename C> __device__ __forceinline__ C w16(C a) {
-    using R = decltype(a.x);
-    constexpr R c1 = R(0.92387953251128675612818318939678828682);  // cos(pi/8)
-    constexpr R s1 = R(0.38268343236508977172845998403039886676);  // sin(pi/8)
-    constexpr R r2 = R(0.70710678118654752440084436210484903928);  // cos(pi/4)
     if constexpr (J == 0) return a;
     else if constexpr (J == 4) return mul_mi(a);
-    else if constexpr (J == 2) return mk<C>((a.x + a.y) * r2, (a.y - a.x) * r2);
-    else if constexpr (J == 6) return mk<C>((a.y - a.x) * r2, -(a.x + a.y) * r2);
-    else if constexpr (J == 1) return mk<C>(fmar(a.x, c1, a.y * s1), fmar(a.y, c1, -(a.x * s1)));
-    else if constexpr (J == 3) return mk<C>(fmar(a.x, s1, a.y * c1), fmar(a.y, s1, -(a.x * c1)));
-    else if constexpr (J == 5) return mk<C>(fmar(a.y, c1, -(a.x * s1)), -fmar(a.y, s1, a.x * c1));
-    else return mk<C>(fmar(a.y, s1, -(a.x * c1)), -fmar(a.y, c1, a.x * s1));   // J == 7
+    else if constexpr (J == 2) return mk<C>(kmul<K_R2>(a.x + a.y), kmul<K_R2>(a.y - a.x));
+    else if constexpr (J == 6) return mk<C>(kmul<K_R2>(a.y - a.x), -kmul<K_R2>(a.x + a.y));
+    else if constexpr (J == 1) return mk<C>(kdot<K_C1, K_S1>(a.x, a.y), kdot<K_C1, K_S1>(a.y, -a.x));
+    else if constexpr (J == 3) return mk<C>(kdot<K_S1, K_C1>(a.x, a.y), kdot<K_S1, K_C1>(a.y, -a.x));
+    else if constexpr (J == 5) return mk<C>(kdot<K_C1, K_S1>(a.y, -a.x), -kdot<K_S1, K_C1>(a.y, a.x));
+    else return mk<C>(kdot<K_S1, K_C1>(a.y, -a.x), -kdot<K_C1, K_S1>(a.y, a.x));   // J == 7
 }
+
+// Stage-twiddle table entries: FP32 keeps (re_hi, im_hi, re_lo, im_lo) of
+// exp(-2 pi i e/n) formed in FP64 (16 bytes, one vector load); FP64 keeps the
+// value.
+__device__ __forceinline__ float2 cmul_tw(float2 x, float4 w) {
+    return mk<float2>(fmar(x.x, w.x, fmar(-x.y, w.y, fmar(x.x, w.z, -(x.y * w.w)))),
+                      fmar(x.x, w.y, fmar(x.y, w.x, fmar(x.x, w.w, x.y * w.z))));
+}
+__device__ __forceinline__ double2 cmul_tw(double2 x, double2 w) { return cmul(x, w); }
 
 template <int R> struct Dft;
 
@@ -92,13 +129,12 @@ template <int R> struct Dft {
         } else if constexpr (R == 3) {
             using T = decltype(x[0].x);
             constexpr T h = T(0.5);
-            constexpr T r3 = T(0.86602540378443864676372317075293618347);  // sin(pi/3)
             const C a = x[0];
             const C s = cadd(x[1], x[2]);
             const C d = csub(x[1], x[2]);
             x[0] = cadd(a, s);
             const C m = mk<C>(fmar(-h, s.x, a.x), fmar(-h, s.y, a.y));
-            const C u = cscale(d, r3);
+            const C u = mk<C>(kmul<K_R3>(d.x), kmul<K_R3>(d.y));   // d sin(pi/3)
             x[1] = mk<C>(m.x + u.y, m.y - u.x);  // m - i u
             x[2] = mk<C>(m.x - u.y, m.y + u.x);  // m + i u
         } else {
@@ -210,9 +246,14 @@ template <typename C, int WP, int SH, int LM> struct LayStrided {
 
 template <typename C> __device__ __forceinline__ C ldg_c(const C *p) { return __ldg(p); }
 
+template <typename C> struct TwFor;
+template <> struct TwFor<float2> { using type = float4; };
+template <> struct TwFor<double2> { using type = double2; };
+template <typename C> using tw_t = typename TwFor<C>::type;
+
 // One Stockham stage (see the header comment).  tw: W_n^e table.
 template <typename C, int N, int E, int S, typename Lay>
-__device__ __forceinline__ void fft_stage(C (&v)[E], const Lay &lay, int t, const C *__restrict__ tw) {
+__device__ __forceinline__ void fft_stage(C (&v)[E], const Lay &lay, int t, const tw_t<C> *__restrict__ tw) {
     constexpr StagePlan P = make_plan(N, E);
     constexpr int R = P.R[S];
     constexpr int NS = P.NS[S];
@@ -230,7 +271,7 @@ __device__ __forceinline__ void fft_stage(C (&v)[E], const Lay &lay, int t, cons
         if constexpr (NS > 1) {
             constexpr int STEP = N / (NS * R);
 #pragma unroll
-            for (int r = 1; r < R; ++r) x[r] = cmul(x[r], ldg_c(tw + k * r * STEP));
+            for (int r = 1; r < R; ++r) x[r] = cmul_tw(x[r], __ldg(tw + k * r * STEP));
         }
         Dft<R>::run(x);
         if constexpr (LAST) {
@@ -248,7 +289,7 @@ __device__ __forceinline__ void fft_stage(C (&v)[E], const Lay &lay, int t, cons
 // and out.  Every thread of the CTA must call it (it contains barriers).
 template <typename C, int N, int E, int NC, int S, typename Lay>
 __device__ __forceinline__ void fft_forward_from(C (&v)[NC][E], const Lay (&lay)[NC], int t,
-                                                 const C *__restrict__ tw) {
+                                                 const tw_t<C> *__restrict__ tw) {
     constexpr StagePlan P = make_plan(N, E);
     if constexpr (S < P.S) {
 #pragma unroll
@@ -268,7 +309,7 @@ __device__ __forceinline__ void fft_forward_from(C (&v)[NC][E], const Lay (&lay)
 
 template <typename C, int N, int E, int NC, typename Lay>
 __device__ __forceinline__ void fft_forward(C (&v)[NC][E], const Lay (&lay)[NC], int t,
-                                            const C *__restrict__ tw) {
+                                            const tw_t<C> *__restrict__ tw) {
     fft_forward_from<C, N, E, NC, 0>(v, lay, t, tw);
 }
 
@@ -282,7 +323,7 @@ template <typename C, int E, int NC> __device__ __forceinline__ void conj_all(C 
 // dir < 0: forward DFT; dir > 0: inverse DFT without the 1/n factor.
 template <typename C, int N, int E, int NC, typename Lay>
 __device__ __forceinline__ void fft_dir(C (&v)[NC][E], const Lay (&lay)[NC], int t,
-                                        const C *__restrict__ tw, int dir) {
+                                        const tw_t<C> *__restrict__ tw, int dir) {
     if (dir > 0) conj_all<C, E, NC>(v);
     fft_forward<C, N, E, NC>(v, lay, t, tw);
     if (dir > 0) conj_all<C, E, NC>(v);

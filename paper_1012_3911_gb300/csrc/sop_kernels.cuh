@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(PassCfg<Real, N, NC, CONTIG>::THREADS)
         coff[1] = (int64_t)a.pair_comp[blockIdx.z][1] * a.comp_stride;
     }
     C *psi = reinterpret_cast<C *>(a.psi);
-    const C *tw = reinterpret_cast<const C *>(a.tw);
+    const tw_t<C> *tw = reinterpret_cast<const tw_t<C> *>(a.tw);
 
     C v[NC][E];
 #pragma unroll
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(Geometry<N, 1>::T) fso1d_kernel(const __grid_c
     const int t = threadIdx.x;
     const int64_t row = blockIdx.x;
     C *psi = reinterpret_cast<C *>(a.psi) + row * N;
-    const C *tw = reinterpret_cast<const C *>(a.tw);
+    const tw_t<C> *tw = reinterpret_cast<const tw_t<C> *>(a.tw);
     const C *vh = reinterpret_cast<const C *>(a.vhalf);
     const C *vf = reinterpret_cast<const C *>(a.vfull);
     const C *ft = reinterpret_cast<const C *>(a.ftab);

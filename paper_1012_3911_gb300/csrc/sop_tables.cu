@@ -45,8 +45,12 @@ __global__ void k_twiddles(void *out, int n, bool f64) {
     if (x > 1.0) x -= 2.0;
     double s, c;
     sincospi(x, &s, &c);
-    if (f64) reinterpret_cast<double2 *>(out)[e] = make_double2(c, -s);
-    else reinterpret_cast<float2 *>(out)[e] = make_float2((float)c, (float)(-s));
+    if (f64) {
+        reinterpret_cast<double2 *>(out)[e] = make_double2(c, -s);
+    } else {
+        const float ch = (float)c, sh = (float)(-s);
+        reinterpret_cast<float4 *>(out)[e] = make_float4(ch, sh, (float)(c - (double)ch), (float)(-s - (double)sh));
+    }
 }
 
 // exp(-i factor V_j), the merged or half real-space factor of Eq. 11 / 22

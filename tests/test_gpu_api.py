@@ -96,6 +96,13 @@ def test_profiling_counts_passes():
     ms, n = sop.sop_profile_read(prop.plan)
     assert n[0] == 6 and n[1] == 5          # real-space passes n+1, momentum passes n
     assert all(t >= 0 for t in ms) and ms[0] > 0 and ms[1] > 0
+    # the counter counts kernels; a profiled set-up bracket may hold several
+    assert sop.sop_launch_counter(prop.plan) - before >= sum(n)
+    sop.sop_profile_read(prop.plan)
+    before = sop.sop_launch_counter(prop.plan)
+    prop.step(5, w.dt, w.field)               # tables for this dt exist now
+    ms, n = sop.sop_profile_read(prop.plan)
+    assert n[4] == 1                          # one field-table build per chunk
     assert sop.sop_launch_counter(prop.plan) - before == sum(n)
 
 
