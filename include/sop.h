@@ -146,6 +146,31 @@ int sop_profile_read(sop_plan plan, double *ms, int64_t *launches, int max_class
  * (passes, table set-up and reductions).  Host-side counter; no sync. */
 int64_t sop_launch_counter(sop_plan plan);
 
+/* Norm without any device allocation.  Not part of the paper's method (it
+ * has no counterpart there); it serves callers that may not allocate device
+ * memory: programs whose own pool allocator owns all of HBM and forbids
+ * other allocations, and latency-bound loops where cudaMalloc/cudaFree, which
+ * can synchronise the whole device, would stall other streams.  Unlike
+ * sop_norm it needs no plan.
+ *   psi_dev   device pointer to n_values complex values (dtype SOP_C64 or
+ *             SOP_C128), aligned to the complex size.
+ *   out_dev   device pointer to one double; receives scale * sum |psi|^2,
+ *             accumulated in FP64 (scale = dV gives the norm of sop_norm).
+ *   cuda_stream  the stream the work is enqueued on (NULL: legacy default).
+ * Asynchronous; the result is ready when the stream reaches it.  Calls no
+ * cudaMalloc, cudaFree or allocating library routine: the block partial sums
+ * live in a fixed array inside the library (256 KB on every GPU that loads
+ * it, held until the process exits), so n_values is limited to 2^29;
+ * larger inputs return SOP_EUNSUPPORTED.  Every slot the reduction reads is
+ * written earlier in the same call, so nothing needs clearing between calls,
+ * but all calls share the array: calls that may overlap on the GPU (unordered
+ * streams or several host threads) race and must be serialised.  The first
+ * call on each device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  Returns
+ * SOP_EINVAL for null or misaligned pointers, a bad dtype or n_values < 0. */
+int sop_norm_noalloc(const void *psi_dev, int64_t n_values, int dtype, double scale, double *out_dev,
+                     void *cuda_stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *sop_last_error(void);
 

@@ -34,6 +34,7 @@ UNITS = [
     ("tables", "sop_tables.cu", []),
     ("reduce", "sop_reduce.cu", []),
     ("api", "sop_api.cu", []),
+    ("noalloc", "sop_noalloc.cu", []),
 ]
 
 

@@ -501,6 +501,10 @@ int read_result(sop_plan p, int count, double *out) {
 
 }  // namespace
 
+namespace sop {
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace sop
+
 extern "C" {
 
 int sop_version(void) { return 1; }

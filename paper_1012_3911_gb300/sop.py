@@ -201,6 +201,20 @@ def sop_launch_counter(plan: int) -> int:
     return int(load().sop_launch_counter(plan))
 
 
+def sop_norm_noalloc(psi, n_values: int, dtype: int, scale: float, out, stream=None) -> None:
+    """Asynchronous norm without device allocation: writes scale * sum |psi|^2
+    into the one-element float64 CUDA tensor ``out``.  ``psi`` is a CUDA
+    tensor or a raw device pointer holding n_values complex values."""
+    lib = load()
+    fn = lib.sop_norm_noalloc
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                   ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    ptr = psi if isinstance(psi, int) else psi.data_ptr()
+    optr = out if isinstance(out, int) else out.data_ptr()
+    _check(fn(ptr, int(n_values), int(dtype), float(scale), optr, _stream_handle(stream)))
+
+
 class Propagator:
     """A plan plus its bound torch state.
 
