@@ -90,9 +90,10 @@ int sop_plan_create(sop_plan *out, int ndim, const int64_t *dims, const double *
 int sop_plan_destroy(sop_plan plan);
 
 /* Bind the wave function: psi_dev is a device pointer to components *
- * prod(dims) complex values of the plan's dtype, aligned to the complex
- * size.  The plan borrows it; the caller keeps it alive while the plan
- * steps.  sop_step updates it in place. */
+ * prod(dims) complex values of the plan's dtype, 16-byte aligned (the pass
+ * kernels copy rows and tiles of it with bulk asynchronous copies).  The
+ * plan borrows it; the caller keeps it alive while the plan steps.  sop_step
+ * updates it in place.  Returns SOP_EINVAL for a NULL or misaligned pointer. */
 int sop_bind_state(sop_plan plan, void *psi_dev);
 
 /* Set the potential energy V (= q*phi of Eqs. 10a/18a, without the laser

@@ -2,11 +2,12 @@
 // one dtype (-DSOP_REAL=float|double, with -DSOP_IS_DOUBLE=1 for double); the
 // double build also defines the pass-geometry query and the shared-memory
 // attribute helper.
+#include <map>
 #include <mutex>
 #include <set>
 #include <utility>
 
-#include "sop_kernels.cuh"
+#include "sop_async.cuh"
 
 #ifndef SOP_REAL
 #error "SOP_REAL must be defined"
@@ -59,6 +60,51 @@ bool pass_geometry(bool f64, int n, int nc, bool contig, int *threads, int *penc
         default:
             return false;
     }
+}
+
+namespace {
+template <typename Real, int N> int async_wp_of(int nc, bool contig) {
+    if (nc == 1) return contig ? AsyncCfg<Real, N, 1, true>::WP : AsyncCfg<Real, N, 1, false>::WP;
+    return contig ? AsyncCfg<Real, N, 2, true>::WP : AsyncCfg<Real, N, 2, false>::WP;
+}
+}  // namespace
+
+int async_pencils_per_cta(bool f64, int n, int nc, bool contig) {
+    switch (n) {
+#define SOP_CASE(N) \
+    case N:         \
+        return f64 ? async_wp_of<double, N>(nc, contig) : async_wp_of<float, N>(nc, contig);
+        SOP_SIZES(SOP_CASE)
+#undef SOP_CASE
+        default:
+            return 0;
+    }
+}
+
+cudaError_t persistent_grid(const void *kern, int threads, size_t smem, int *blocks_per_sm, int *sms) {
+    // Resident CTAs per SM and SM count, cached per (kernel, device).
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, std::pair<int, int>> cache;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find({kern, dev});
+    if (it != cache.end()) {
+        *blocks_per_sm = it->second.first;
+        *sms = it->second.second;
+        return cudaSuccess;
+    }
+    int nb = 0, ns = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&ns, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (nb < 1) nb = 1;
+    cache[{kern, dev}] = {nb, ns};
+    *blocks_per_sm = nb;
+    *sms = ns;
+    return cudaSuccess;
 }
 
 cudaError_t ensure_smem_attr(const void *kern, int bytes) {

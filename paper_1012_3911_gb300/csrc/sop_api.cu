@@ -12,9 +12,13 @@
 //           inverse FFT_y
 // so a 2D step costs two passes over psi and a 3D step four.  In 1D a single
 // kernel keeps the line on chip for many steps.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <mutex>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -90,6 +94,15 @@ struct sop_plan_s {
     double *host_result = nullptr;  // pinned, 4 doubles
     double *pgrid = nullptr;
     void *scratch = nullptr;
+
+    int *errflag = nullptr;         // device word set by kernels whose bounded waits gave up
+    bool async_passes = true;       // persistent passes with bulk / TMA prefetch
+    struct MapEntry {
+        void *ptr;
+        int axis, nc;
+        TensorMapBytes map;
+    };
+    std::vector<MapEntry> maps;     // tensor maps of psi / scratch per strided axis
 
     bool prof = false;
     std::vector<EventPair> events;
@@ -203,6 +216,7 @@ int plan_free(sop_plan p) {
     dfree(p->result);
     dfree(p->pgrid);
     dfree(p->scratch);
+    dfree(p->errflag);
     if (p->host_stage) cudaFreeHost(p->host_stage);
     if (p->host_result) cudaFreeHost(p->host_result);
     if (p->stage_done) cudaEventDestroy(p->stage_done);
@@ -215,10 +229,100 @@ int plan_free(sop_plan p) {
     return SOP_OK;
 }
 
-cudaError_t launch_pass(sop_plan p, const PassArgs &a, int nc) {
-    const bool contig = a.axis == 0;
-    if (p->f64) return contig ? launch_pass_f64_contig(a, nc, p->stream) : launch_pass_f64_strided(a, nc, p->stream);
-    return contig ? launch_pass_f32_contig(a, nc, p->stream) : launch_pass_f32_strided(a, nc, p->stream);
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+int largest_divisor_le_host(int n, int cap) {
+    int d = n < cap ? n : cap;
+    while (n % d != 0) --d;
+    return d;
+}
+
+// 4D (3D for 2D lattices) tensor map of an array of p->comps components over
+// the lattice, in 8-byte elements (a c64 value or half a c128 value), with a
+// box of the async pass's pencils-per-CTA along x, up to 256 points along the
+// pass axis and one along the rest.
+int tensor_map(sop_plan p, void *base, int axis, int nc, TensorMapBytes *out) {
+    for (auto &m : p->maps)
+        if (m.ptr == base && m.axis == axis && m.nc == nc) {
+            *out = m.map;
+            return SOP_OK;
+        }
+    auto enc = tensor_map_encoder();
+    if (!enc) return fail(SOP_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const int k = p->f64 ? 2 : 1;
+    const int n = (int)p->dims[axis];
+    const int wp = async_pencils_per_cta(p->f64, n, nc, false);
+    if (wp <= 0) return fail(SOP_EUNSUPPORTED, "no asynchronous pass for this size");
+    const int rank = p->ndim + 1;
+    cuuint64_t gdim[5] = {1, 1, 1, 1, 1}, gstride[4] = {0, 0, 0, 0};
+    cuuint32_t box[5] = {1, 1, 1, 1, 1}, estr[5] = {1, 1, 1, 1, 1};
+    gdim[0] = (cuuint64_t)p->dims[0] * k;
+    box[0] = (cuuint32_t)(wp * k);
+    uint64_t bytes = (uint64_t)p->dims[0] * p->csz;
+    for (int d = 1; d < p->ndim; ++d) {
+        gdim[d] = (cuuint64_t)p->dims[d];
+        box[d] = d == axis ? (cuuint32_t)largest_divisor_le_host(n, 256) : 1;
+        gstride[d - 1] = bytes;
+        bytes *= (uint64_t)p->dims[d];
+    }
+    gdim[p->ndim] = (cuuint64_t)p->comps;
+    gstride[p->ndim - 1] = bytes;
+    CUtensorMap map;
+    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, (cuuint32_t)rank, base, gdim, gstride, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(SOP_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    sop_plan_s::MapEntry ent;
+    ent.ptr = base;
+    ent.axis = axis;
+    ent.nc = nc;
+    std::memcpy(ent.map.b, &map, sizeof(map));
+    if (p->maps.size() >= 16) p->maps.erase(p->maps.begin());
+    p->maps.push_back(ent);
+    *out = ent.map;
+    return SOP_OK;
+}
+
+// Launch one pass: the persistent asynchronous kernel when it exists for the
+// size, else the one-shot kernel.  Returns a sop_status.
+int launch_pass(sop_plan p, const PassArgs &a0, int nc, const char *what) {
+    const bool contig = a0.axis == 0;
+    if (p->async_passes) {
+        PassArgs a = a0;
+        a.errflag = p->errflag;
+        a.n_comp_total = p->comps;
+        TensorMapBytes tm;
+        std::memset(&tm, 0, sizeof(tm));
+        const int wp = async_pencils_per_cta(p->f64, (int)p->dims[a.axis], nc, contig);
+        if (wp > 0) {
+            if (!contig) {
+                int rc = tensor_map(p, a.psi, a.axis, nc, &tm);
+                if (rc) return rc;
+            }
+            cudaError_t e;
+            if (p->f64) e = contig ? launch_async_f64_contig(a, nc, tm, p->stream) : launch_async_f64_strided(a, nc, tm, p->stream);
+            else e = contig ? launch_async_f32_contig(a, nc, tm, p->stream) : launch_async_f32_strided(a, nc, tm, p->stream);
+            if (e == cudaSuccess) return SOP_OK;
+            if (e != cudaErrorInvalidValue) return cuda_fail(e, what);
+            cudaGetLastError();   // size without an asynchronous kernel: use the one-shot pass
+        }
+    }
+    cudaError_t e;
+    if (p->f64) e = contig ? launch_pass_f64_contig(a0, nc, p->stream) : launch_pass_f64_strided(a0, nc, p->stream);
+    else e = contig ? launch_pass_f32_contig(a0, nc, p->stream) : launch_pass_f32_strided(a0, nc, p->stream);
+    return e == cudaSuccess ? SOP_OK : cuda_fail(e, what);
 }
 
 void base_args(sop_plan p, PassArgs &a, void *psi, int axis) {
@@ -234,6 +338,10 @@ void base_args(sop_plan p, PassArgs &a, void *psi, int axis) {
     a.axis = axis;
     for (int b = 0; b < 3; ++b) a.dims[b] = b < p->ndim ? p->dims[b] : 1;
     a.tw = p->tw[axis];
+    // strided tiles: element stride of the coordinate that is neither x nor the axis
+    a.o_stride = 0;
+    if (p->ndim == 3 && axis == 1) a.o_stride = p->dims[0] * p->dims[1];
+    if (p->ndim == 3 && axis == 2) a.o_stride = p->dims[0];
     a.scale_hi = p->scale_hi;
     a.scale_lo = p->scale_lo;
     a.pair_comp[0][0] = 0;
@@ -244,9 +352,22 @@ void base_args(sop_plan p, PassArgs &a, void *psi, int axis) {
 
 int run_pass(sop_plan p, const PassArgs &a, int nc, int cls, const char *what) {
     Bracket br(p, cls);
-    cudaError_t e = launch_pass(p, a, nc);
-    if (e != cudaSuccess) return cuda_fail(e, what);
+    int rc = launch_pass(p, a, nc, what);
+    if (rc) return rc;
     br.done();
+    return SOP_OK;
+}
+
+// SOP_ETIMEOUT if a kernel's bounded wait gave up since the last check
+// (call only after synchronising the plan stream).
+int check_errflag(sop_plan p) {
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, p->errflag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(error flag)");
+    if (h != 0) {
+        cudaMemset(p->errflag, 0, sizeof(int));
+        return fail(SOP_ETIMEOUT, "a pass kernel gave up waiting for its tile copies (bounded wait)");
+    }
     return SOP_OK;
 }
 
@@ -496,7 +617,7 @@ int read_result(sop_plan p, int count, double *out) {
     e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     for (int i = 0; i < count; ++i) out[i] = p->host_result[i];
-    return SOP_OK;
+    return check_errflag(p);
 }
 
 }  // namespace
@@ -544,6 +665,10 @@ int sop_plan_create(sop_plan *out, int ndim, const int64_t *dims, const double *
     p->prm = prm;
     p->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     p->csz = p->f64 ? 16 : 8;
+    {
+        const char *env = std::getenv("SOP_PASSES");   // "sync": one-shot passes (for comparisons)
+        p->async_passes = !(env && std::string(env) == "sync");
+    }
     p->npts = 1;
     for (int a = 0; a < ndim; ++a) p->npts *= dims[a];
     cudaError_t e = cudaGetDevice(&p->device);
@@ -580,6 +705,11 @@ int sop_plan_create(sop_plan *out, int ndim, const int64_t *dims, const double *
     if (!rc) rc = dalloc(&p->partial, (size_t)reduce_blocks() * sizeof(double), "partials");
     if (!rc) rc = dalloc(&p->result, 4 * sizeof(double), "result");
     if (!rc) rc = dalloc(&p->pgrid, (size_t)sum_n * sizeof(double), "momenta");
+    if (!rc) rc = dalloc(&p->errflag, sizeof(int), "error flag");
+    if (!rc) {
+        e = cudaMemsetAsync(p->errflag, 0, sizeof(int), p->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync(error flag)");
+    }
     if (!rc) {
         p->row_len = sum_n;
         rc = dalloc(&p->ftab, (size_t)kFieldChunk * sum_n * p->csz, "field tables");
@@ -622,8 +752,8 @@ int sop_plan_destroy(sop_plan plan) { return plan_free(plan); }
 int sop_bind_state(sop_plan p, void *psi_dev) {
     if (!p) return fail(SOP_EINVAL, "sop_bind_state: null plan");
     if (!psi_dev) return fail(SOP_EINVAL, "sop_bind_state: psi is NULL");
-    if (reinterpret_cast<uintptr_t>(psi_dev) % p->csz != 0)
-        return fail(SOP_EINVAL, "sop_bind_state: psi is not aligned to the complex size");
+    if (reinterpret_cast<uintptr_t>(psi_dev) % 16 != 0)
+        return fail(SOP_EINVAL, "sop_bind_state: psi must be 16-byte aligned");
     p->psi = psi_dev;
     return SOP_OK;
 }
@@ -664,7 +794,7 @@ int sop_step_host(sop_plan p, void *psi_host, int64_t n_steps, double dt, const 
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(D2H)");
     e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-    return SOP_OK;
+    return check_errflag(p);
 }
 
 int sop_norm(sop_plan p, double *out) {
@@ -744,7 +874,7 @@ int sop_profile_read(sop_plan p, double *ms, int64_t *launches, int max_classes)
         p->event_pool.push_back(ep.b);
     }
     p->events.clear();
-    return SOP_OK;
+    return check_errflag(p);
 }
 
 int64_t sop_launch_counter(sop_plan p) { return p ? p->launches : 0; }

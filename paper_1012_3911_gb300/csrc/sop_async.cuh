@@ -1,0 +1,472 @@
+// sop_async.cuh -- persistent pencil passes with asynchronous tile prefetch.
+//
+// Same arithmetic as pass_kernel (sop_kernels.cuh): load a group of pencils,
+// [transform] -> pointwise factor -> [transform], store in place.  The
+// difference is how data reaches shared memory.  Each CTA loops over tiles
+// (persistent grid sized to the GPU) and keeps two tile buffers: while it
+// transforms tile k in one buffer, the copy engine fills the other with tile
+// k+1:
+//   axis 0 (rows contiguous):  cp.async.bulk of each row
+//   strided axes:              cp.async.bulk.tensor (TMA) 3D/4D boxes of
+//                              W adjacent pencils x <=256 points
+// Completion is tracked with mbarrier transaction counts.  The tile buffer is
+// also the Stockham exchange buffer, so a pencil is read from HBM once and
+// never staged through registers before its first stage.  The stage
+// twiddles (a per-stage table, built once per CTA) and the factor table of
+// the pass axis (the laser-phase row of the real-space pass or the kinetic
+// row of the momentum pass, copied once per launch) live in shared memory;
+// the per-point phase values of the real-space pass are fetched into
+// registers at the start of each tile, bypassing L1.
+//
+// Every wait on an mbarrier is bounded in wall time (globaltimer).  If a wait
+// gives up, the CTA agrees on it with a block vote, sets bit 0 of *errflag,
+// waits (again bounded) for copies it still has in flight, and returns; the
+// host reports SOP_ETIMEOUT at its next synchronising call.
+#pragma once
+
+#include <cuda.h>
+
+#include "sop_kernels.cuh"
+
+namespace sop {
+
+// ---------------------------------------------------------------------------
+// PTX wrappers (sm_90 and later)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase with the given parity to complete, at most limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s: far beyond any tile copy
+
+__host__ __device__ constexpr int largest_divisor_le(int n, int cap) {
+    int d = n < cap ? n : cap;
+    while (n % d != 0) --d;
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// Geometry
+// ---------------------------------------------------------------------------
+
+template <typename Real, int N, int NC, bool CONTIG> struct AsyncCfg {
+    using G = Geometry<N, NC>;
+    using C = cplx_t<Real>;
+    static constexpr int E = G::E;
+    static constexpr int T = G::T;
+    static constexpr int CSZ = 2 * (int)sizeof(Real);
+    static constexpr int PITCH = ((N + (N >> G::LR)) + 1) & ~1;   // even: rows stay 16-byte aligned
+    static constexpr int wp_contig() {
+        int w = 256 / T;
+        return w < 1 ? 1 : w;
+    }
+    static constexpr int wp_strided() {
+        const int wmin = CSZ == 8 ? 2 : 1;                 // a TMA box row is at least 16 bytes
+        int w = (32 * 1024) / (NC * N * CSZ);              // ~32 KB per tile buffer
+        const int wmax = CSZ == 8 ? 128 : 64;              // box row <= 256 8-byte elements
+        if (w > wmax) w = wmax;
+        int p = 1;
+        while (p * 2 <= w) p *= 2;
+        w = p;
+        while (w > wmin && w * T > 512) w /= 2;
+        return w < wmin ? wmin : w;
+    }
+    static constexpr int WP = CONTIG ? wp_contig() : wp_strided();
+    static constexpr int THREADS = T * WP;
+    static constexpr int BR = largest_divisor_le(N, 256);   // box extent along the axis
+    static constexpr size_t al128(size_t x) { return (x + 127) & ~size_t(127); }
+    static constexpr size_t BUF = al128(CONTIG ? (size_t)WP * NC * PITCH * CSZ : (size_t)NC * N * WP * CSZ);
+    static constexpr size_t TWZ = al128((size_t)StageTable<C, N, E>::ENTRIES * CSZ + 16);
+    static constexpr size_t AXT = al128((size_t)N * CSZ);   // pass-axis table (field row / kinetic row)
+    static constexpr size_t OFF_BUF = 128, OFF_TWZ = OFF_BUF + 2 * BUF, OFF_AXT = OFF_TWZ + TWZ;
+    static constexpr size_t SMEM = OFF_AXT + AXT;
+    static constexpr bool FITS = SMEM <= 227 * 1024 && THREADS <= 1024;
+    // CTAs per SM that shared memory allows; the register budget follows.
+    static constexpr int minb() {
+        int b = (int)((227 * 1024) / (SMEM > 0 ? SMEM : 1));
+        const int bt = 2048 / THREADS;
+        const int br = 65536 / (THREADS * 104);   // leave ~104 registers per thread
+        if (bt < b) b = bt;
+        if (br < b) b = br;
+        if (b > 8) b = 8;
+        return b < 1 ? 1 : b;
+    }
+    static constexpr int MINB = minb();
+    static constexpr int ROWLINES = (128 / (WP * CSZ)) < 1 ? 1 : 128 / (WP * CSZ);
+    static constexpr int LM = ROWLINES - 1;
+    static constexpr int SH = G::LR > ilog2c(ROWLINES) ? G::LR : ilog2c(ROWLINES);
+};
+
+// ---------------------------------------------------------------------------
+// The kernel
+// ---------------------------------------------------------------------------
+
+template <typename Real, int N, int NC, bool CONTIG>
+__global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncCfg<Real, N, NC, CONTIG>::MINB)
+    pass_kernel_async(const __grid_constant__ PassArgs a, const __grid_constant__ CUtensorMap tmap) {
+    using Cfg = AsyncCfg<Real, N, NC, CONTIG>;
+    using C = cplx_t<Real>;
+    using Ph = Phase<Real>;
+    constexpr int E = Cfg::E, T = Cfg::T, WP = Cfg::WP, CSZ = Cfg::CSZ;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);   // 0, 1: tile buffers; 2: axis table
+    unsigned char *const buf0 = smem + Cfg::OFF_BUF;       // tile buffer b starts at buf0 + b * BUF
+    C *twz = reinterpret_cast<C *>(smem + Cfg::OFF_TWZ);   // per-stage twiddles
+    C *axt = reinterpret_cast<C *>(smem + Cfg::OFF_AXT);   // pass-axis factor table
+
+    const int t = CONTIG ? threadIdx.x : threadIdx.y;   // thread within the pencil
+    const int w = CONTIG ? threadIdx.y : threadIdx.x;   // pencil within the tile
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int pz = NC == 2 ? (int)blockIdx.z : 0;
+    const int64_t stride = CONTIG ? 1 : a.stride;
+    const bool op_v = a.op == OP_V, op_t = a.op == OP_T;
+    const bool want_v = CONTIG && a.vtab != nullptr && (op_v || a.op == OP_DV);
+    // the factor table of this pass's axis (field row for OP_V, kinetic row for OP_T)
+    const C *axsrc = nullptr;
+    if (NC == 1 && (op_v || op_t)) {
+        const void *p = op_v ? (a.axis == 0 ? a.ftab[0] : (a.axis == 1 ? a.ftab[1] : a.ftab[2]))
+                             : (a.axis == 0 ? a.ttab[0] : (a.axis == 1 ? a.ttab[1] : a.ttab[2]));
+        axsrc = reinterpret_cast<const C *>(p);
+    }
+    C *psi = reinterpret_cast<C *>(a.psi);
+    const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]), barx = smem_addr(&bars[2]);
+
+    const int64_t ntiles = a.n_tiles;
+    int64_t tile = blockIdx.x;
+    if (tile >= ntiles) return;
+
+    if (tid == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+        mbar_init(barx, 1);
+        fence_mbar_init();
+    }
+    StageTable<C, N, E>::fill(twz, reinterpret_cast<const C *>(a.tw), tid, Cfg::THREADS);
+    __syncthreads();
+
+    const int64_t per_batch = a.n_pencils;
+    const int64_t total = (NC == 1) ? per_batch * a.n_batch : per_batch;
+    const int64_t n0 = a.dims[0];
+    const int64_t tiles_per_batch = CONTIG ? 0 : a.n_xgroups * (per_batch / n0);
+
+    auto comp_index = [&](int c, int64_t b) -> int64_t {
+        return NC == 1 ? b : (int64_t)a.pair_comp[pz][c];
+    };
+
+    // Thread 0: start the copies of tile tl into buffer slot b.
+    auto issue = [&](int64_t tl, int b) {
+        const uint32_t bar = b ? bar1 : bar0;
+        const uint32_t dst0 = smem_addr(buf0 + b * Cfg::BUF);
+        if constexpr (CONTIG) {
+            const int64_t p0 = tl * WP;
+            const int rows = (int)((total - p0) < WP ? (total - p0) : WP);
+            mbar_expect_tx(bar, (uint32_t)(rows * NC * N * CSZ));
+            for (int r = 0; r < rows; ++r) {
+                const int64_t p = p0 + r;
+                int64_t bidx = 0, pp = p;
+                if (NC == 1) {
+                    bidx = p / per_batch;
+                    pp = p - bidx * per_batch;
+                }
+                for (int c = 0; c < NC; ++c) {
+                    const int64_t off = comp_index(c, bidx) * a.comp_stride + pp * N;
+                    bulk_g2s(dst0 + (uint32_t)((r * NC + c) * Cfg::PITCH * CSZ), psi + off, (uint32_t)(N * CSZ), bar);
+                }
+            }
+        } else {
+            const int64_t bidx = NC == 1 ? tl / tiles_per_batch : 0;
+            const int64_t rem = NC == 1 ? tl - bidx * tiles_per_batch : tl;
+            const int64_t o = rem / a.n_xgroups;
+            const int64_t xg = rem - o * a.n_xgroups;
+            const int x0 = (int)(xg * WP) * (CSZ / 8);
+            mbar_expect_tx(bar, (uint32_t)(NC * N * WP * CSZ));
+            for (int c = 0; c < NC; ++c) {
+                const int cc = (int)comp_index(c, bidx);
+                for (int r = 0; r < N / Cfg::BR; ++r) {
+                    const uint32_t dst = dst0 + (uint32_t)((c * N + r * Cfg::BR) * WP * CSZ);
+                    if (a.ndim == 2) {
+                        tma_load_3d(dst, &tmap, x0, r * Cfg::BR, cc, bar);
+                    } else if (a.axis == 1) {
+                        tma_load_4d(dst, &tmap, x0, r * Cfg::BR, (int)o, cc, bar);
+                    } else {
+                        tma_load_4d(dst, &tmap, x0, (int)o, r * Cfg::BR, cc, bar);
+                    }
+                }
+            }
+        }
+    };
+    // A wait gave up: record it, drain what this CTA still has in flight, leave.
+    auto give_up = [&](int it, bool cur_pending, bool next_issued, bool ax_pending) {
+        if (tid == 0) {
+            atomicOr(a.errflag, 1);
+            const int b = it & 1;
+            if (cur_pending) mbar_wait_bounded(b ? bar1 : bar0, (it >> 1) & 1, kWaitLimitNs);
+            if (next_issued) mbar_wait_bounded(b ? bar0 : bar1, ((it + 1) >> 1) & 1, kWaitLimitNs);
+            if (ax_pending) mbar_wait_bounded(barx, 0, kWaitLimitNs);
+        }
+    };
+
+    const bool has_axt = axsrc != nullptr;
+    if (tid == 0) {
+        if (has_axt) {
+            mbar_expect_tx(barx, (uint32_t)(N * CSZ));
+            bulk_g2s(smem_addr(axt), axsrc, (uint32_t)(N * CSZ), barx);
+        }
+        issue(tile, 0);
+    }
+    if (has_axt) {
+        const bool okx = mbar_wait_bounded(barx, 0, kWaitLimitNs);
+        if (!__syncthreads_and(okx)) {
+            give_up(0, true, false, true);
+            return;
+        }
+    }
+    const C *tw = twz;
+
+    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+        const int b = it & 1;
+        const int64_t next = tile + gridDim.x;
+        const bool has_next = next < ntiles;
+        if (tid == 0) {
+            fence_proxy_async_smem();   // earlier generic accesses to the buffers precede the copies
+            if (has_next) issue(next, b ^ 1);
+        }
+
+        // Pencil of this thread.
+        int64_t base, coff[NC];
+        bool active;
+        if constexpr (CONTIG) {
+            const int64_t p = tile * WP + w;
+            active = p < total;
+            const int64_t pc = active ? p : 0;
+            int64_t bidx = 0, pp = pc;
+            if (NC == 1) {
+                bidx = pc / per_batch;
+                pp = pc - bidx * per_batch;
+            }
+            base = pp * N;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) coff[c] = comp_index(c, bidx) * a.comp_stride;
+        } else {
+            const int64_t bidx = NC == 1 ? tile / tiles_per_batch : 0;
+            const int64_t rem = NC == 1 ? tile - bidx * tiles_per_batch : tile;
+            const int64_t o = rem / a.n_xgroups;
+            const int64_t x = (rem - o * a.n_xgroups) * WP + w;
+            active = x < n0;
+            base = (active ? x : 0) + o * a.o_stride;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) coff[c] = comp_index(c, bidx) * a.comp_stride;
+        }
+
+        // Per-point phase values of this pencil, fetched now and used after
+        // the first transform (bypassing L1).
+        C vpre[E];
+        if (want_v) {
+            const C *vt = reinterpret_cast<const C *>(a.vtab) + base;
+#pragma unroll
+            for (int m = 0; m < E; ++m) vpre[m] = ld_stream(vt + (t + T * m));
+        }
+
+        bool ok = mbar_wait_bounded(b ? bar1 : bar0, (it >> 1) & 1, kWaitLimitNs);
+        if (!__syncthreads_and(ok)) {
+            give_up(it, true, has_next, false);
+            return;
+        }
+
+        // Registers <- tile buffer (landing layout), then the buffer becomes
+        // the exchange buffer.
+        C *bufc = reinterpret_cast<C *>(buf0 + b * Cfg::BUF);
+        C v[NC][E];
+        using LayC = LayContig<C, Cfg::G::LR>;
+        using LayS = LayStrided<C, WP, Cfg::SH, Cfg::LM>;
+        using Lay = typename std::conditional<CONTIG, LayC, LayS>::type;
+        Lay lay[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            if constexpr (CONTIG) {
+                C *row = bufc + (w * NC + c) * Cfg::PITCH;
+                lay[c].p = row;
+#pragma unroll
+                for (int m = 0; m < E; ++m) v[c][m] = row[t + T * m];
+            } else {
+                C *col = bufc + c * N * WP + w;
+                lay[c].p = col;
+#pragma unroll
+                for (int m = 0; m < E; ++m) v[c][m] = col[(t + T * m) * WP];
+            }
+        }
+        __syncthreads();
+
+        if (a.pre != 0) fft_dir<C, N, E, NC, true>(v, lay, t, tw, a.pre);
+
+        if constexpr (NC == 1) {
+            if (op_v || op_t) {
+                // Pencil-constant part from the other axes' tables, per-point part
+                // from the axis table in shared memory (and the phase values).
+                const C *tab[3];
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax)
+                    tab[ax] = reinterpret_cast<const C *>(op_v ? a.ftab[ax] : a.ttab[ax]);
+                int co[3];
+                unravel3(base, a.dims, a.ndim, co);
+                C g = Ph::one();
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax)
+                    if (ax < a.ndim && ax != a.axis && tab[ax] != nullptr) g = Ph::combine(g, ldg_c(tab[ax] + co[ax]));
+                const Real shi = Real(a.scale_hi), slo = Real(a.scale_lo);
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const int i = t + T * m;
+                    C f = g;
+                    if (has_axt) f = Ph::combine(axt[i], f);
+                    if (op_v) {
+                        if (want_v) f = Ph::combine(vpre[m], f);
+                        v[0][m] = Ph::apply(v[0][m], f);
+                    } else {
+                        v[0][m] = scale2(Ph::apply(v[0][m], f), shi, slo);
+                    }
+                }
+            }
+        } else {
+            if (a.op == OP_DV) {
+                // (psi_a, psi_b) <- exp(-i V tau') M (psi_a, psi_b) on this component pair
+                const double *mx = a.mix[pz];
+                const C m00 = mk<C>(Real(mx[0]), Real(mx[1])), m01 = mk<C>(Real(mx[2]), Real(mx[3]));
+                const C m10 = mk<C>(Real(mx[4]), Real(mx[5])), m11 = mk<C>(Real(mx[6]), Real(mx[7]));
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    C u0 = cadd(cmul(m00, v[0][m]), cmul(m01, v[1][m]));
+                    C u1 = cadd(cmul(m10, v[0][m]), cmul(m11, v[1][m]));
+                    if (want_v) {
+                        u0 = Ph::apply(u0, vpre[m]);
+                        u1 = Ph::apply(u1, vpre[m]);
+                    }
+                    v[0][m] = u0;
+                    v[1][m] = u1;
+                }
+            } else {
+                apply_op<Real, E, T, NC>(v, a, base, stride, t, pz, nullptr, 1);
+            }
+        }
+
+        if (a.post != 0) {
+            if (a.pre != 0) __syncthreads();
+            fft_dir<C, N, E, NC, true>(v, lay, t, tw, a.post);
+        }
+
+        if (active) {
+            const int64_t step = (int64_t)T * stride;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                C *q = psi + coff[c] + base + (int64_t)t * stride;
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    st_stream(q, v[c][m]);
+                    q += step;
+                }
+            }
+        }
+        __syncthreads();   // the tile buffer is free again
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launcher
+// ---------------------------------------------------------------------------
+
+cudaError_t ensure_smem_attr(const void *kern, int bytes);
+cudaError_t persistent_grid(const void *kern, int threads, size_t smem, int *blocks_per_sm, int *sms);
+
+template <typename Real, int N, int NC, bool CONTIG>
+cudaError_t launch_async_t(const PassArgs &a0, const TensorMapBytes &tm, cudaStream_t s) {
+    using Cfg = AsyncCfg<Real, N, NC, CONTIG>;
+    if constexpr (!Cfg::FITS) {
+        return cudaErrorInvalidValue;
+    } else {
+        PassArgs a = a0;
+        const int64_t total = (NC == 1) ? a.n_pencils * a.n_batch : a.n_pencils;
+        if (CONTIG) {
+            a.n_xgroups = 0;
+            a.n_tiles = (total + Cfg::WP - 1) / Cfg::WP;
+        } else {
+            const int64_t n0 = a.dims[0];
+            a.n_xgroups = (n0 + Cfg::WP - 1) / Cfg::WP;
+            const int64_t others = a.n_pencils / n0;
+            a.n_tiles = a.n_xgroups * others * (NC == 1 ? a.n_batch : 1);
+        }
+        if (a.n_tiles <= 0) return cudaSuccess;
+        auto kern = pass_kernel_async<Real, N, NC, CONTIG>;
+        cudaError_t e = ensure_smem_attr(reinterpret_cast<const void *>(kern), (int)Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, sms = 0;
+        e = persistent_grid(reinterpret_cast<const void *>(kern), Cfg::THREADS, Cfg::SMEM, &per_sm, &sms);
+        if (e != cudaSuccess) return e;
+        int64_t blocks = (int64_t)per_sm * sms;
+        if (blocks > a.n_tiles) blocks = a.n_tiles;
+        if (blocks < 1) blocks = 1;
+        dim3 grid((unsigned)blocks, 1, NC == 2 ? 2 : 1);
+        dim3 block = CONTIG ? dim3(Cfg::T, Cfg::WP, 1) : dim3(Cfg::WP, Cfg::T, 1);
+        kern<<<grid, block, Cfg::SMEM, s>>>(a, *reinterpret_cast<const CUtensorMap *>(tm.b));
+        return cudaGetLastError();
+    }
+}
+
+}  // namespace sop

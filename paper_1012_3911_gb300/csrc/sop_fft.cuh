@@ -19,14 +19,17 @@
 //  * The inverse transform is conj(F(conj(x))): only the forward code is
 //    compiled.
 //  * Stage twiddles come from a per-size table W_n^e, e < n, formed in FP64
-//    on the device; the FP32 table keeps each value as an unevaluated sum
-//    hi + lo, and the constants inside the radix-3/4/8/16 butterflies are
-//    applied the same way (see kmul below), so no rounded constant biases
-//    the modulus of a transform.
+//    on the device (FP32 keeps z = w - 1, see tw_apply); each thread loads only
+//    its R-1 distinct twiddles per stage (StageTw).  Constants inside the
+//    radix-3/4/8/16 butterflies and the compile-time roots that complete the
+//    stage twiddles are applied as hi + lo in FP32 (kmul, rot48), so no
+//    rounded constant biases the modulus of a transform.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 namespace sop {
 
@@ -98,14 +101,75 @@ template <int J, typename C> __device__ __forceinline__ C w16(C a) {
     else return mk<C>(kdot<K_S1, K_C1>(a.y, -a.x), -kdot<K_C1, K_S1>(a.y, a.x));   // J == 7
 }
 
-// Stage-twiddle table entries: FP32 keeps (re_hi, im_hi, re_lo, im_lo) of
-// exp(-2 pi i e/n) formed in FP64 (16 bytes, one vector load); FP64 keeps the
-// value.
-__device__ __forceinline__ float2 cmul_tw(float2 x, float4 w) {
-    return mk<float2>(fmar(x.x, w.x, fmar(-x.y, w.y, fmar(x.x, w.z, -(x.y * w.w)))),
-                      fmar(x.x, w.y, fmar(x.y, w.x, fmar(x.x, w.w, x.y * w.z))));
+// Stage twiddles.  FP32 stores z = w - 1 of w = exp(-2 pi i e/n) (formed in
+// FP64, rounded once) and applies x + z x: the same four FMAs as a complex
+// product, but twiddles near 1 -- the ones a smooth field's energy flows
+// through -- keep their full relative precision, so their rounding does not
+// bias the norm.  FP64 stores and multiplies w.
+__device__ __forceinline__ float2 tw_apply(float2 x, float2 z) {
+    return mk<float2>(fmar(z.x, x.x, fmar(-z.y, x.y, x.x)), fmar(z.x, x.y, fmar(z.y, x.x, x.y)));
 }
-__device__ __forceinline__ double2 cmul_tw(double2 x, double2 w) { return cmul(x, w); }
+__device__ __forceinline__ double2 tw_apply(double2 x, double2 w) { return cmul(x, w); }
+
+// cos(2 pi j / 48) for any integer j (first-quadrant decimal expansions and
+// symmetry); used only in constant expressions.
+__host__ __device__ constexpr double cos48(int j) {
+    const double q[13] = {1.0,
+                          0.99144486137381041114455752692856287128,
+                          0.96592582628906828674974319972889736763,
+                          0.92387953251128675612818318939678828682,
+                          0.86602540378443864676372317075293618347,
+                          0.79335334029123516457977696150129927663,
+                          0.70710678118654752440084436210484903928,
+                          0.60876142900872063941609754289816400452,
+                          0.5,
+                          0.38268343236508977172845998403039886676,
+                          0.25881904510252076234889883762404832835,
+                          0.13052619222005159154840622789548901019,
+                          0.0};
+    j %= 48;
+    if (j < 0) j += 48;
+    if (j <= 12) return q[j];
+    if (j <= 24) return -q[24 - j];
+    if (j <= 36) return -q[j - 24];
+    return q[48 - j];
+}
+__host__ __device__ constexpr double sin48(int j) { return cos48(j - 12); }
+
+// x * exp(-2 pi i J / 48) with the constant applied as hi + lo in FP32.
+template <int J> __device__ __forceinline__ float2 rot48(float2 x) {
+    constexpr int j = ((J % 48) + 48) % 48;
+    if constexpr (j == 0) return x;
+    else if constexpr (j == 12) return mul_mi(x);
+    else if constexpr (j == 24) return mk<float2>(-x.x, -x.y);
+    else if constexpr (j == 36) return mul_pi(x);
+    else {
+        constexpr double c = cos48(j), s = sin48(j);
+        constexpr float ch = (float)c, cl = (float)(c - (double)ch);
+        constexpr float sh = (float)s, sl = (float)(s - (double)sh);
+        return mk<float2>(fmar(x.x, ch, fmar(x.y, sh, fmar(x.x, cl, x.y * sl))),
+                          fmar(x.y, ch, fmar(-x.x, sh, fmar(x.y, cl, -(x.x * sl)))));
+    }
+}
+template <int J> __device__ __forceinline__ double2 rot48(double2 x) {
+    constexpr int j = ((J % 48) + 48) % 48;
+    if constexpr (j == 0) return x;
+    else if constexpr (j == 12) return mul_mi(x);
+    else if constexpr (j == 24) return mk<double2>(-x.x, -x.y);
+    else if constexpr (j == 36) return mul_pi(x);
+    else {
+        constexpr double c = cos48(j), s = sin48(j);
+        return mk<double2>(fmar(x.x, c, x.y * s), fmar(x.y, c, -(x.x * s)));
+    }
+}
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I in [B, E).
+template <int B, int E, typename F> __device__ __forceinline__ void sfor(F &&f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        sfor<B + 1, E>(f);
+    }
+}
 
 template <int R> struct Dft;
 
@@ -246,14 +310,73 @@ template <typename C, int WP, int SH, int LM> struct LayStrided {
 
 template <typename C> __device__ __forceinline__ C ldg_c(const C *p) { return __ldg(p); }
 
-template <typename C> struct TwFor;
-template <> struct TwFor<float2> { using type = float4; };
-template <> struct TwFor<double2> { using type = double2; };
-template <typename C> using tw_t = typename TwFor<C>::type;
+// Stage twiddles of one thread.  In stage s (radix R, Ns = product of the
+// earlier radices) butterfly j = t + T q multiplies input r by
+// W_{Ns R}^{(j mod Ns) r}.  Either Ns divides T, and j mod Ns = t mod Ns for
+// every q, or T divides Ns, and W_{Ns R}^{(j mod Ns) r} =
+// W_{Ns R}^{t r} W_{Ns R / T}^{(q mod Ns/T) r}, the second factor a root of
+// unity of an order dividing E, known at compile time.  So a thread loads only
+// W_{Ns R}^{(t mod Ns) r}, r = 1..R-1, per stage (fetched one stage ahead,
+// before the exchange barrier, so the load latency overlaps the barrier).
+template <typename C, int N, int E, int S> struct StageTw {
+    static constexpr StagePlan P = make_plan(N, E);
+    static constexpr int R = (S < P.S) ? P.R[S] : 2;
+    static constexpr int NS = (S < P.S) ? P.NS[S] : 1;
+    static constexpr int T = N / E;
+    C z[R > 1 ? R - 1 : 1];
+    // tab: the full W_n table in global memory, or (SMEM) this size's
+    // per-stage table in shared memory (see StageTable).
+    template <bool SMEM>
+    __device__ __forceinline__ void load(const C *__restrict__ tab, int t);
+};
 
-// One Stockham stage (see the header comment).  tw: W_n^e table.
+// Per-stage twiddle table laid out for conflict-free shared-memory reads:
+// stage s (s >= 1) holds W_{Ns R}^{k r} at off(s) + (r - 1) KS + k for
+// k < KS = min(Ns, T), r = 1..R-1; thread t reads k = t mod KS.
+template <typename C, int N, int E> struct StageTable {
+    static constexpr StagePlan P = make_plan(N, E);
+    static constexpr int T = N / E;
+    static constexpr int ks(int s) { return P.NS[s] < T ? P.NS[s] : T; }
+    static constexpr int off(int s) {
+        int o = 0;
+        for (int i = 1; i < s; ++i) o += (P.R[i] - 1) * ks(i);
+        return o;
+    }
+    static constexpr int ENTRIES = off(P.S);
+    // Fill from the global W_n table; all nthreads threads of the CTA call it.
+    __device__ __forceinline__ static void fill(C *dst, const C *__restrict__ tab, int tid, int nthreads) {
+        sfor<1, P.S>([&](auto sc) {
+            constexpr int S = decltype(sc)::value;
+            constexpr int KS = ks(S), OFF = off(S), R = P.R[S], STEP = N / (P.NS[S] * P.R[S]);
+            for (int loc = tid; loc < (R - 1) * KS; loc += nthreads) {
+                const int k = loc % KS, r = loc / KS + 1;
+                dst[OFF + loc] = ldg_c(tab + k * r * STEP);
+            }
+        });
+    }
+};
+
+template <typename C, int N, int E, int S>
+template <bool SMEM>
+__device__ __forceinline__ void StageTw<C, N, E, S>::load(const C *__restrict__ tab, int t) {
+    if constexpr (S > 0 && S < P.S) {
+        static_assert(NS % T == 0 || T % NS == 0, "stage twiddles must split");
+        if constexpr (SMEM) {
+            constexpr int KS = StageTable<C, N, E>::ks(S), OFF = StageTable<C, N, E>::off(S);
+            const int k = t % KS;
+#pragma unroll
+            for (int r = 1; r < R; ++r) z[r - 1] = tab[OFF + (r - 1) * KS + k];
+        } else {
+            const int k = t % NS;
+#pragma unroll
+            for (int r = 1; r < R; ++r) z[r - 1] = ldg_c(tab + k * r * (N / (NS * R)));
+        }
+    }
+}
+
+// One Stockham stage (see the header comment).
 template <typename C, int N, int E, int S, typename Lay>
-__device__ __forceinline__ void fft_stage(C (&v)[E], const Lay &lay, int t, const tw_t<C> *__restrict__ tw) {
+__device__ __forceinline__ void fft_stage(C (&v)[E], const Lay &lay, int t, const StageTw<C, N, E, S> &tw) {
     constexpr StagePlan P = make_plan(N, E);
     constexpr int R = P.R[S];
     constexpr int NS = P.NS[S];
@@ -261,56 +384,67 @@ __device__ __forceinline__ void fft_stage(C (&v)[E], const Lay &lay, int t, cons
     constexpr int Q = E / R;
     constexpr bool LAST = (S == P.S - 1);
     static_assert(E % R == 0, "radix must divide E");
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
+    sfor<0, Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
         const int j = t + T * q;
-        const int k = j % NS;
         C x[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = v[q + r * Q];
         if constexpr (NS > 1) {
-            constexpr int STEP = N / (NS * R);
-#pragma unroll
-            for (int r = 1; r < R; ++r) x[r] = cmul_tw(x[r], __ldg(tw + k * r * STEP));
+            sfor<1, R>([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                x[r] = tw_apply(x[r], tw.z[r - 1]);
+                if constexpr (NS > T) {
+                    constexpr int M = NS / T;           // distinct j mod Ns per thread
+                    constexpr int O = NS * R / T;       // order of the extra root
+                    static_assert(48 % O == 0, "root order");
+                    x[r] = rot48<((q % M) * r % O) * (48 / O)>(x[r]);
+                }
+            });
         }
         Dft<R>::run(x);
         if constexpr (LAST) {
 #pragma unroll
             for (int r = 0; r < R; ++r) v[q + r * Q] = x[r];
         } else {
+            const int k = j % NS;
             const int ob = (j / NS) * NS * R + k;
 #pragma unroll
             for (int r = 0; r < R; ++r) lay.st(ob + r * NS, x[r]);
         }
-    }
+    });
 }
 
 // Forward FFT of NC pencils held by this thread group, natural mapping in
 // and out.  Every thread of the CTA must call it (it contains barriers).
-template <typename C, int N, int E, int NC, int S, typename Lay>
-__device__ __forceinline__ void fft_forward_from(C (&v)[NC][E], const Lay (&lay)[NC], int t,
-                                                 const tw_t<C> *__restrict__ tw) {
+// tw holds the twiddles of stage S; those of stage S+1 are fetched before the
+// exchange barrier.
+template <typename C, int N, int E, int NC, int S, bool SMEM, typename Lay>
+__device__ __forceinline__ void fft_forward_from(C (&v)[NC][E], const Lay (&lay)[NC], int t, const C *__restrict__ tab,
+                                                 const StageTw<C, N, E, S> &tw) {
     constexpr StagePlan P = make_plan(N, E);
     if constexpr (S < P.S) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) fft_stage<C, N, E, S>(v[c], lay[c], t, tw);
         if constexpr (S + 1 < P.S) {
             constexpr int T = N / E;
+            StageTw<C, N, E, S + 1> nxt;
+            nxt.template load<SMEM>(tab, t);
             __syncthreads();
 #pragma unroll
             for (int c = 0; c < NC; ++c)
 #pragma unroll
                 for (int m = 0; m < E; ++m) v[c][m] = lay[c].ld(t + T * m);
             __syncthreads();
+            fft_forward_from<C, N, E, NC, S + 1, SMEM>(v, lay, t, tab, nxt);
         }
-        fft_forward_from<C, N, E, NC, S + 1>(v, lay, t, tw);
     }
 }
 
-template <typename C, int N, int E, int NC, typename Lay>
-__device__ __forceinline__ void fft_forward(C (&v)[NC][E], const Lay (&lay)[NC], int t,
-                                            const tw_t<C> *__restrict__ tw) {
-    fft_forward_from<C, N, E, NC, 0>(v, lay, t, tw);
+template <typename C, int N, int E, int NC, bool SMEM = false, typename Lay>
+__device__ __forceinline__ void fft_forward(C (&v)[NC][E], const Lay (&lay)[NC], int t, const C *__restrict__ tab) {
+    StageTw<C, N, E, 0> none;
+    fft_forward_from<C, N, E, NC, 0, SMEM>(v, lay, t, tab, none);
 }
 
 template <typename C, int E, int NC> __device__ __forceinline__ void conj_all(C (&v)[NC][E]) {
@@ -321,11 +455,11 @@ template <typename C, int E, int NC> __device__ __forceinline__ void conj_all(C 
 }
 
 // dir < 0: forward DFT; dir > 0: inverse DFT without the 1/n factor.
-template <typename C, int N, int E, int NC, typename Lay>
-__device__ __forceinline__ void fft_dir(C (&v)[NC][E], const Lay (&lay)[NC], int t,
-                                        const tw_t<C> *__restrict__ tw, int dir) {
+template <typename C, int N, int E, int NC, bool SMEM = false, typename Lay>
+__device__ __forceinline__ void fft_dir(C (&v)[NC][E], const Lay (&lay)[NC], int t, const C *__restrict__ tw,
+                                        int dir) {
     if (dir > 0) conj_all<C, E, NC>(v);
-    fft_forward<C, N, E, NC>(v, lay, t, tw);
+    fft_forward<C, N, E, NC, SMEM>(v, lay, t, tw);
     if (dir > 0) conj_all<C, E, NC>(v);
 }
 

@@ -43,6 +43,12 @@ struct PassArgs {
     // OP_DV: 2x2 complex block per component pair (re, im of m00, m01, m10, m11)
     double mix[2][8];
     int pair_comp[2][2];     // component indices of each pair
+    // Persistent asynchronous passes (filled by the launcher)
+    int *errflag;            // device word; bit 1 set when a bounded wait gave up
+    int64_t n_tiles;         // tiles of the pass (per component pair for nc == 2)
+    int64_t n_xgroups;       // strided: tiles along x
+    int64_t o_stride;        // strided: element stride of the remaining coordinate
+    int n_comp_total;        // components in the array (tensor-map outer extent)
 };
 
 // Arguments of the one-dimensional whole-step kernel.
@@ -67,6 +73,17 @@ cudaError_t launch_pass_f32_contig(const PassArgs &a, int nc, cudaStream_t s);
 cudaError_t launch_pass_f32_strided(const PassArgs &a, int nc, cudaStream_t s);
 cudaError_t launch_pass_f64_contig(const PassArgs &a, int nc, cudaStream_t s);
 cudaError_t launch_pass_f64_strided(const PassArgs &a, int nc, cudaStream_t s);
+// Persistent passes with asynchronous (bulk / TMA) prefetch of the next tile.
+// tmap: the 4D tensor map of psi for strided axes (ignored for axis 0).
+struct TensorMapBytes {
+    alignas(64) unsigned char b[128];
+};
+cudaError_t launch_async_f32_contig(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s);
+cudaError_t launch_async_f32_strided(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s);
+cudaError_t launch_async_f64_contig(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s);
+cudaError_t launch_async_f64_strided(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s);
+// Pencils per CTA of the asynchronous pass (the tensor-map box width for strided axes).
+int async_pencils_per_cta(bool f64, int n, int nc, bool contig);
 cudaError_t launch_1d_f32(const Args1D &a, int n, cudaStream_t s);
 cudaError_t launch_1d_f64(const Args1D &a, int n, cudaStream_t s);
 // Threads and dynamic shared memory of the pass kernel for (dtype, n, nc, contig).

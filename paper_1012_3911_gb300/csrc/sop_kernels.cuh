@@ -95,6 +95,108 @@ __device__ __forceinline__ void unravel3(int64_t lin, const int64_t *dims, int n
     }
 }
 
+// Pointwise factor of a pass on the E values per component a thread holds
+// (axis index i = t + T m of the pencil starting at linear point index base).
+// vrow/vstride: the per-point phase values of this pencil (global or shared
+// memory), or null.  pz: component pair (nc == 2).
+// Loads and stores that bypass L1 but keep the normal L2 policy: psi and the
+// per-point tables stream through each pass once and must not push the
+// twiddle and field tables out of L1, while psi should stay in L2 for the
+// next pass.
+template <typename C> __device__ __forceinline__ C ld_stream(const C *p) { return __ldcg(p); }
+template <typename C> __device__ __forceinline__ void st_stream(C *p, C v) { __stcg(p, v); }
+
+// VGLOBAL: vrow points to global memory (read with ld_stream); otherwise it
+// points to shared memory.
+template <typename Real, int E, int T, int NC, bool VGLOBAL = false>
+__device__ __forceinline__ void apply_op(cplx_t<Real> (&v)[NC][E], const PassArgs &a, int64_t base, int64_t stride,
+                                         int t, int pz, const cplx_t<Real> *vrow, int64_t vstride) {
+    using C = cplx_t<Real>;
+    using Ph = Phase<Real>;
+    if constexpr (NC == 1) {
+        if (a.op == OP_V || a.op == OP_T) {
+            // Pencil-constant part: factors of the axes other than this one.
+            const bool is_v = a.op == OP_V;
+            const C *tab[3];
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) tab[ax] = reinterpret_cast<const C *>(is_v ? a.ftab[ax] : a.ttab[ax]);
+            int co[3];
+            unravel3(base, a.dims, a.ndim, co);
+            C g = Ph::one();
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax)
+                if (ax < a.ndim && ax != a.axis && tab[ax] != nullptr) g = Ph::combine(g, ldg_c(tab[ax] + co[ax]));
+            const C *ta = a.axis == 0 ? tab[0] : (a.axis == 1 ? tab[1] : tab[2]);
+            const C *vt = vrow;
+            const Real shi = Real(a.scale_hi), slo = Real(a.scale_lo);
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int i = t + T * m;
+                C f = g;
+                if (ta != nullptr) f = Ph::combine(ldg_c(ta + i), f);
+                if (is_v) {
+                    if (vt != nullptr) {
+                        const C vv = VGLOBAL ? ld_stream(vt + (int64_t)i * vstride) : vt[(int64_t)i * vstride];
+                        f = Ph::combine(vv, f);
+                    }
+                    v[0][m] = Ph::apply(v[0][m], f);
+                } else {
+                    v[0][m] = scale2(Ph::apply(v[0][m], f), shi, slo);
+                }
+            }
+        }
+    } else {
+        if (a.op == OP_DV) {
+            // (psi_a, psi_b) <- exp(-i V tau') M (psi_a, psi_b), M the 2x2 block of
+            // the spinor-mixing factor on this component pair.
+            const double *mx = a.mix[pz];
+            const C m00 = mk<C>(Real(mx[0]), Real(mx[1])), m01 = mk<C>(Real(mx[2]), Real(mx[3]));
+            const C m10 = mk<C>(Real(mx[4]), Real(mx[5])), m11 = mk<C>(Real(mx[6]), Real(mx[7]));
+            const C *vt = vrow;
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int i = t + T * m;
+                C u0 = cadd(cmul(m00, v[0][m]), cmul(m01, v[1][m]));
+                C u1 = cadd(cmul(m10, v[0][m]), cmul(m11, v[1][m]));
+                if (vt != nullptr) {
+                    const C f = VGLOBAL ? ld_stream(vt + (int64_t)i * vstride) : vt[(int64_t)i * vstride];
+                    u0 = Ph::apply(u0, f);
+                    u1 = Ph::apply(u1, f);
+                }
+                v[0][m] = u0;
+                v[1][m] = u1;
+            }
+        } else if (a.op == OP_DT) {
+            // U = cos(th) - i sin(th) H/E on the pair, H/E = [[mu, k],[k*, -mu]] with
+            // k = kappa* on pair (1,4) and k = kappa on pair (2,3), kappa = c(p_x + i p_y)/E;
+            // table entry q = (cos th, sin th mu, sin th c p_x/E, sin th c p_y/E).
+            const C *dt2 = reinterpret_cast<const C *>(a.dtab);
+            const Real sgn = pz == 0 ? Real(1) : Real(-1);
+            const Real shi = Real(a.scale_hi), slo = Real(a.scale_lo);
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int i = t + T * m;
+                const int64_t k = base + (int64_t)i * stride;
+                C q0, q1;
+                if constexpr (sizeof(Real) == 4) {
+                    const float4 q = __ldcg(reinterpret_cast<const float4 *>(dt2) + k);
+                    q0 = mk<C>(q.x, q.y);
+                    q1 = mk<C>(q.z, q.w);
+                } else {
+                    q0 = ld_stream(dt2 + 2 * k);
+                    q1 = ld_stream(dt2 + 2 * k + 1);
+                }
+                const C u00 = mk<C>(q0.x, -q0.y), u11 = mk<C>(q0.x, q0.y);
+                const C u01 = mk<C>(-sgn * q1.y, -q1.x), u10 = mk<C>(sgn * q1.y, -q1.x);
+                const C r0 = cadd(cmul(u00, v[0][m]), cmul(u01, v[1][m]));
+                const C r1 = cadd(cmul(u10, v[0][m]), cmul(u11, v[1][m]));
+                v[0][m] = scale2(r0, shi, slo);
+                v[1][m] = scale2(r1, shi, slo);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // The pass kernel
 // ---------------------------------------------------------------------------
@@ -135,14 +237,14 @@ __global__ void __launch_bounds__(PassCfg<Real, N, NC, CONTIG>::THREADS)
         coff[1] = (int64_t)a.pair_comp[blockIdx.z][1] * a.comp_stride;
     }
     C *psi = reinterpret_cast<C *>(a.psi);
-    const tw_t<C> *tw = reinterpret_cast<const tw_t<C> *>(a.tw);
+    const C *tw = reinterpret_cast<const C *>(a.tw);
 
     C v[NC][E];
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
         for (int m = 0; m < E; ++m)
-            v[c][m] = active ? psi[coff[c] + base + (int64_t)(t + T * m) * stride] : mk<C>(Real(0), Real(0));
+            v[c][m] = active ? ld_stream(psi + coff[c] + base + (int64_t)(t + T * m) * stride) : mk<C>(Real(0), Real(0));
 
     // Exchange layouts, one per component.
     using LayC = LayContig<C, Cfg::G::LR>;
@@ -157,86 +259,7 @@ __global__ void __launch_bounds__(PassCfg<Real, N, NC, CONTIG>::THREADS)
 
     if (a.pre != 0) fft_dir<C, N, E, NC>(v, lay, t, tw, a.pre);
 
-    // ---- pointwise factor -------------------------------------------------
-    if constexpr (NC == 1) {
-        if (a.op == OP_V || a.op == OP_T) {
-            // Pencil-constant part: factors of the axes other than this one.
-            const bool is_v = a.op == OP_V;
-            const C *tab[3];
-#pragma unroll
-            for (int ax = 0; ax < 3; ++ax) tab[ax] = reinterpret_cast<const C *>(is_v ? a.ftab[ax] : a.ttab[ax]);
-            int co[3];
-            unravel3(base, a.dims, a.ndim, co);
-            C g = Ph::one();
-#pragma unroll
-            for (int ax = 0; ax < 3; ++ax)
-                if (ax < a.ndim && ax != a.axis && tab[ax] != nullptr) g = Ph::combine(g, ldg_c(tab[ax] + co[ax]));
-            const C *ta = a.axis == 0 ? tab[0] : (a.axis == 1 ? tab[1] : tab[2]);
-            const C *vt = reinterpret_cast<const C *>(a.vtab);
-            const Real shi = Real(a.scale_hi), slo = Real(a.scale_lo);
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const int i = t + T * m;
-                C f = g;
-                if (ta != nullptr) f = Ph::combine(ldg_c(ta + i), f);
-                if (is_v) {
-                    if (vt != nullptr) f = Ph::combine(ldg_c(vt + base + (int64_t)i * stride), f);
-                    v[0][m] = Ph::apply(v[0][m], f);
-                } else {
-                    v[0][m] = scale2(Ph::apply(v[0][m], f), shi, slo);
-                }
-            }
-        }
-    } else {
-        if (a.op == OP_DV) {
-            // (psi_a, psi_b) <- exp(-i V tau') M (psi_a, psi_b), M the 2x2 block of
-            // the spinor-mixing factor on this component pair.
-            const double *mx = a.mix[blockIdx.z];
-            const C m00 = mk<C>(Real(mx[0]), Real(mx[1])), m01 = mk<C>(Real(mx[2]), Real(mx[3]));
-            const C m10 = mk<C>(Real(mx[4]), Real(mx[5])), m11 = mk<C>(Real(mx[6]), Real(mx[7]));
-            const C *vt = reinterpret_cast<const C *>(a.vtab);
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const int i = t + T * m;
-                C u0 = cadd(cmul(m00, v[0][m]), cmul(m01, v[1][m]));
-                C u1 = cadd(cmul(m10, v[0][m]), cmul(m11, v[1][m]));
-                if (vt != nullptr) {
-                    const C f = ldg_c(vt + base + (int64_t)i * stride);
-                    u0 = Ph::apply(u0, f);
-                    u1 = Ph::apply(u1, f);
-                }
-                v[0][m] = u0;
-                v[1][m] = u1;
-            }
-        } else if (a.op == OP_DT) {
-            // U = cos(th) - i sin(th) H/E on the pair, H/E = [[mu, k],[k*, -mu]] with
-            // k = kappa* on pair (1,4) and k = kappa on pair (2,3), kappa = c(p_x + i p_y)/E;
-            // table entry q = (cos th, sin th mu, sin th c p_x/E, sin th c p_y/E).
-            const C *dt2 = reinterpret_cast<const C *>(a.dtab);
-            const Real sgn = blockIdx.z == 0 ? Real(1) : Real(-1);
-            const Real shi = Real(a.scale_hi), slo = Real(a.scale_lo);
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const int i = t + T * m;
-                const int64_t k = base + (int64_t)i * stride;
-                C q0, q1;
-                if constexpr (sizeof(Real) == 4) {
-                    const float4 q = __ldg(reinterpret_cast<const float4 *>(dt2) + k);
-                    q0 = mk<C>(q.x, q.y);
-                    q1 = mk<C>(q.z, q.w);
-                } else {
-                    q0 = ldg_c(dt2 + 2 * k);
-                    q1 = ldg_c(dt2 + 2 * k + 1);
-                }
-                const C u00 = mk<C>(q0.x, -q0.y), u11 = mk<C>(q0.x, q0.y);
-                const C u01 = mk<C>(-sgn * q1.y, -q1.x), u10 = mk<C>(sgn * q1.y, -q1.x);
-                const C r0 = cadd(cmul(u00, v[0][m]), cmul(u01, v[1][m]));
-                const C r1 = cadd(cmul(u10, v[0][m]), cmul(u11, v[1][m]));
-                v[0][m] = scale2(r0, shi, slo);
-                v[1][m] = scale2(r1, shi, slo);
-            }
-        }
-    }
+    apply_op<Real, E, T, NC, true>(v, a, base, stride, t, blockIdx.z, reinterpret_cast<const cplx_t<Real> *>(a.vtab) + (a.vtab ? base : 0), stride);
 
     if (a.post != 0) {
         if (a.pre != 0) __syncthreads();   // the exchange buffer is reused
@@ -247,7 +270,7 @@ __global__ void __launch_bounds__(PassCfg<Real, N, NC, CONTIG>::THREADS)
 #pragma unroll
         for (int c = 0; c < NC; ++c)
 #pragma unroll
-            for (int m = 0; m < E; ++m) psi[coff[c] + base + (int64_t)(t + T * m) * stride] = v[c][m];
+            for (int m = 0; m < E; ++m) st_stream(psi + coff[c] + base + (int64_t)(t + T * m) * stride, v[c][m]);
     }
 }
 
@@ -270,7 +293,7 @@ __global__ void __launch_bounds__(Geometry<N, 1>::T) fso1d_kernel(const __grid_c
     const int t = threadIdx.x;
     const int64_t row = blockIdx.x;
     C *psi = reinterpret_cast<C *>(a.psi) + row * N;
-    const tw_t<C> *tw = reinterpret_cast<const tw_t<C> *>(a.tw);
+    const C *tw = reinterpret_cast<const C *>(a.tw);
     const C *vh = reinterpret_cast<const C *>(a.vhalf);
     const C *vf = reinterpret_cast<const C *>(a.vfull);
     const C *ft = reinterpret_cast<const C *>(a.ftab);

@@ -1,7 +1,7 @@
 // sop_pass_inst.cu -- instantiates the pencil-pass kernels for one dtype and
 // one axis kind.  The build compiles this file four times:
 //   -DSOP_REAL=float|double  -DSOP_CONTIG=1 (axis 0, contiguous) | 0 (strided)
-#include "sop_kernels.cuh"
+#include "sop_async.cuh"
 
 #ifndef SOP_REAL
 #error "SOP_REAL must be defined"
@@ -20,6 +20,7 @@
 #define SOP_SUFFIX_float _f32
 #define SOP_SUFFIX_double _f64
 #define SOP_LAUNCH_NAME SOP_CAT(SOP_CAT(launch_pass, SOP_CAT(SOP_SUFFIX_, SOP_REAL)), SOP_KIND)
+#define SOP_ASYNC_NAME SOP_CAT(SOP_CAT(launch_async, SOP_CAT(SOP_SUFFIX_, SOP_REAL)), SOP_KIND)
 
 #define SOP_SIZES(X) \
     X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024) \
@@ -34,6 +35,20 @@ cudaError_t SOP_LAUNCH_NAME(const PassArgs &a, int nc, cudaStream_t s) {
     case N:                                                                           \
         return nc == 1 ? launch_pass_t<SOP_REAL, N, 1, (SOP_CONTIG != 0)>(a, s)       \
                        : launch_pass_t<SOP_REAL, N, 2, (SOP_CONTIG != 0)>(a, s);
+        SOP_SIZES(SOP_CASE)
+#undef SOP_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t SOP_ASYNC_NAME(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s) {
+    const int n = (int)a.dims[a.axis];
+    switch (n) {
+#define SOP_CASE(N)                                                                           \
+    case N:                                                                                   \
+        return nc == 1 ? launch_async_t<SOP_REAL, N, 1, (SOP_CONTIG != 0)>(a, tmap, s)        \
+                       : launch_async_t<SOP_REAL, N, 2, (SOP_CONTIG != 0)>(a, tmap, s);
         SOP_SIZES(SOP_CASE)
 #undef SOP_CASE
         default:

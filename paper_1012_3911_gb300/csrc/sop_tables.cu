@@ -48,8 +48,10 @@ __global__ void k_twiddles(void *out, int n, bool f64) {
     if (f64) {
         reinterpret_cast<double2 *>(out)[e] = make_double2(c, -s);
     } else {
-        const float ch = (float)c, sh = (float)(-s);
-        reinterpret_cast<float4 *>(out)[e] = make_float4(ch, sh, (float)(c - (double)ch), (float)(-s - (double)sh));
+        // z = w - 1 with Re z = cos - 1 = -2 sin^2(pi x / 2) (no cancellation)
+        double sh, chh;
+        sincospi(0.5 * x, &sh, &chh);
+        reinterpret_cast<float2 *>(out)[e] = make_float2((float)(-2.0 * sh * sh), (float)(-s));
     }
 }
 
