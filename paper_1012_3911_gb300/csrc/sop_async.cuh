@@ -95,6 +95,22 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, int c0, int c1, int c2, uint32_t src) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, int c0, int c1, int c2, int c3, uint32_t src) {
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(map),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// The shared-memory sources of this thread's committed bulk stores have been read.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// This thread's committed bulk stores are complete (globally visible).
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s: far beyond any tile copy
 
 __host__ __device__ constexpr int largest_divisor_le(int n, int cap) {
@@ -133,7 +149,9 @@ template <typename Real, int N, int NC, bool CONTIG> struct AsyncCfg {
     static constexpr int THREADS = T * WP;
     static constexpr int BR = largest_divisor_le(N, 256);   // box extent along the axis
     static constexpr size_t al128(size_t x) { return (x + 127) & ~size_t(127); }
-    static constexpr size_t BUF = al128(CONTIG ? (size_t)WP * NC * PITCH * CSZ : (size_t)NC * N * WP * CSZ);
+    static constexpr size_t LAND = (size_t)NC * N * WP * CSZ;       // strided: TMA landing layout [c][i][w]
+    static constexpr size_t XCHG = (size_t)WP * NC * PITCH * CSZ;   // padded per-pencil exchange rows
+    static constexpr size_t BUF = al128(CONTIG ? XCHG : (LAND > XCHG ? LAND : XCHG));
     static constexpr size_t TWZ = al128((size_t)StageTable<C, N, E>::ENTRIES * CSZ + 16);
     static constexpr size_t AXT = al128((size_t)N * CSZ);   // pass-axis table (field row / kinetic row)
     static constexpr size_t OFF_BUF = 128, OFF_TWZ = OFF_BUF + 2 * BUF, OFF_AXT = OFF_TWZ + TWZ;
@@ -150,9 +168,6 @@ template <typename Real, int N, int NC, bool CONTIG> struct AsyncCfg {
         return b < 1 ? 1 : b;
     }
     static constexpr int MINB = minb();
-    static constexpr int ROWLINES = (128 / (WP * CSZ)) < 1 ? 1 : 128 / (WP * CSZ);
-    static constexpr int LM = ROWLINES - 1;
-    static constexpr int SH = G::LR > ilog2c(ROWLINES) ? G::LR : ilog2c(ROWLINES);
 };
 
 // ---------------------------------------------------------------------------
@@ -172,8 +187,8 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
     C *twz = reinterpret_cast<C *>(smem + Cfg::OFF_TWZ);   // per-stage twiddles
     C *axt = reinterpret_cast<C *>(smem + Cfg::OFF_AXT);   // pass-axis factor table
 
-    const int t = CONTIG ? threadIdx.x : threadIdx.y;   // thread within the pencil
-    const int w = CONTIG ? threadIdx.y : threadIdx.x;   // pencil within the tile
+    const int t = threadIdx.x;   // thread within the pencil
+    const int w = threadIdx.y;   // pencil within the tile
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int pz = NC == 2 ? (int)blockIdx.z : 0;
     const int64_t stride = CONTIG ? 1 : a.stride;
@@ -211,6 +226,24 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         return NC == 1 ? b : (int64_t)a.pair_comp[pz][c];
     };
 
+    // Strided axes: the TMA boxes of tile tl, f(component slot, box, coords...)
+    // with coordinates (x [in 8-byte units], axis 1, axis 2, component).
+    auto tile_boxes = [&](int64_t tl, auto &&f) {
+        const int64_t bidx = NC == 1 ? tl / tiles_per_batch : 0;
+        const int64_t rem = NC == 1 ? tl - bidx * tiles_per_batch : tl;
+        const int64_t o = rem / a.n_xgroups;
+        const int64_t xg = rem - o * a.n_xgroups;
+        const int x0 = (int)(xg * WP) * (CSZ / 8);
+        for (int c = 0; c < NC; ++c) {
+            const int cc = (int)comp_index(c, bidx);
+            for (int r = 0; r < N / Cfg::BR; ++r) {
+                if (a.ndim == 2) f(c, r, x0, r * Cfg::BR, 0, cc);
+                else if (a.axis == 1) f(c, r, x0, r * Cfg::BR, (int)o, cc);
+                else f(c, r, x0, (int)o, r * Cfg::BR, cc);
+            }
+        }
+    };
+
     // Thread 0: start the copies of tile tl into buffer slot b.
     auto issue = [&](int64_t tl, int b) {
         const uint32_t bar = b ? bar1 : bar0;
@@ -232,31 +265,29 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
                 }
             }
         } else {
-            const int64_t bidx = NC == 1 ? tl / tiles_per_batch : 0;
-            const int64_t rem = NC == 1 ? tl - bidx * tiles_per_batch : tl;
-            const int64_t o = rem / a.n_xgroups;
-            const int64_t xg = rem - o * a.n_xgroups;
-            const int x0 = (int)(xg * WP) * (CSZ / 8);
             mbar_expect_tx(bar, (uint32_t)(NC * N * WP * CSZ));
-            for (int c = 0; c < NC; ++c) {
-                const int cc = (int)comp_index(c, bidx);
-                for (int r = 0; r < N / Cfg::BR; ++r) {
-                    const uint32_t dst = dst0 + (uint32_t)((c * N + r * Cfg::BR) * WP * CSZ);
-                    if (a.ndim == 2) {
-                        tma_load_3d(dst, &tmap, x0, r * Cfg::BR, cc, bar);
-                    } else if (a.axis == 1) {
-                        tma_load_4d(dst, &tmap, x0, r * Cfg::BR, (int)o, cc, bar);
-                    } else {
-                        tma_load_4d(dst, &tmap, x0, (int)o, r * Cfg::BR, cc, bar);
-                    }
-                }
-            }
+            tile_boxes(tl, [&](int c, int r, int c0, int c1, int c2, int c3) {
+                const uint32_t dst = dst0 + (uint32_t)((c * N + r * Cfg::BR) * WP * CSZ);
+                if (a.ndim == 2) tma_load_3d(dst, &tmap, c0, c1, c3, bar);
+                else tma_load_4d(dst, &tmap, c0, c1, c2, c3, bar);
+            });
         }
+    };
+    // Thread 0: write tile tl back from buffer slot b (strided axes).
+    auto store_tile = [&](int64_t tl, int b) {
+        const uint32_t src0 = smem_addr(buf0 + b * Cfg::BUF);
+        tile_boxes(tl, [&](int c, int r, int c0, int c1, int c2, int c3) {
+            const uint32_t src = src0 + (uint32_t)((c * N + r * Cfg::BR) * WP * CSZ);
+            if (a.ndim == 2) tma_store_3d(&tmap, c0, c1, c3, src);
+            else tma_store_4d(&tmap, c0, c1, c2, c3, src);
+        });
+        bulk_commit();
     };
     // A wait gave up: record it, drain what this CTA still has in flight, leave.
     auto give_up = [&](int it, bool cur_pending, bool next_issued, bool ax_pending) {
         if (tid == 0) {
             atomicOr(a.errflag, 1);
+            if (!CONTIG) bulk_wait_all();
             const int b = it & 1;
             if (cur_pending) mbar_wait_bounded(b ? bar1 : bar0, (it >> 1) & 1, kWaitLimitNs);
             if (next_issued) mbar_wait_bounded(b ? bar0 : bar1, ((it + 1) >> 1) & 1, kWaitLimitNs);
@@ -286,7 +317,8 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         const int64_t next = tile + gridDim.x;
         const bool has_next = next < ntiles;
         if (tid == 0) {
-            fence_proxy_async_smem();   // earlier generic accesses to the buffers precede the copies
+            if (!CONTIG) bulk_wait_read();   // the tile store out of buffer b ^ 1 has read it
+            fence_proxy_async_smem();        // earlier generic accesses to the buffers precede the copies
             if (has_next) issue(next, b ^ 1);
         }
 
@@ -335,20 +367,17 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         // the exchange buffer.
         C *bufc = reinterpret_cast<C *>(buf0 + b * Cfg::BUF);
         C v[NC][E];
-        using LayC = LayContig<C, Cfg::G::LR>;
-        using LayS = LayStrided<C, WP, Cfg::SH, Cfg::LM>;
-        using Lay = typename std::conditional<CONTIG, LayC, LayS>::type;
+        using Lay = LayContig<C, Cfg::G::LR>;   // exchange rows, one per pencil and component
         Lay lay[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
+            C *row = bufc + (w * NC + c) * Cfg::PITCH;
+            lay[c].p = row;
             if constexpr (CONTIG) {
-                C *row = bufc + (w * NC + c) * Cfg::PITCH;
-                lay[c].p = row;
 #pragma unroll
                 for (int m = 0; m < E; ++m) v[c][m] = row[t + T * m];
             } else {
-                C *col = bufc + c * N * WP + w;
-                lay[c].p = col;
+                const C *col = bufc + c * N * WP + w;   // TMA landing layout [c][i][w]
 #pragma unroll
                 for (int m = 0; m < E; ++m) v[c][m] = col[(t + T * m) * WP];
             }
@@ -412,20 +441,32 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
             fft_dir<C, N, E, NC, true>(v, lay, t, tw, a.post);
         }
 
-        if (active) {
-            const int64_t step = (int64_t)T * stride;
+        if constexpr (CONTIG) {
+            if (active) {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                C *q = psi + coff[c] + base + (int64_t)t * stride;
+                for (int c = 0; c < NC; ++c) {
+                    C *q = psi + coff[c] + base + t;
 #pragma unroll
-                for (int m = 0; m < E; ++m) {
-                    st_stream(q, v[c][m]);
-                    q += step;
+                    for (int m = 0; m < E; ++m) st_stream(q + T * m, v[c][m]);
                 }
             }
+            __syncthreads();   // the tile buffer is free again
+        } else {
+            // Back into the landing layout, then one TMA store per box (clipped at
+            // the lattice edge, so inactive pencils are never written).
+            if (a.pre != 0 || a.post != 0) __syncthreads();   // exchange reads are done
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                C *col = bufc + c * N * WP + w;
+#pragma unroll
+                for (int m = 0; m < E; ++m) col[(t + T * m) * WP] = v[c][m];
+            }
+            fence_proxy_async_smem();   // make these writes visible to the bulk copy engine
+            __syncthreads();
+            if (tid == 0) store_tile(tile, b);
         }
-        __syncthreads();   // the tile buffer is free again
     }
+    if (!CONTIG && tid == 0) bulk_wait_all();   // the last stores are complete before the kernel ends
 }
 
 // ---------------------------------------------------------------------------
@@ -463,7 +504,7 @@ cudaError_t launch_async_t(const PassArgs &a0, const TensorMapBytes &tm, cudaStr
         if (blocks > a.n_tiles) blocks = a.n_tiles;
         if (blocks < 1) blocks = 1;
         dim3 grid((unsigned)blocks, 1, NC == 2 ? 2 : 1);
-        dim3 block = CONTIG ? dim3(Cfg::T, Cfg::WP, 1) : dim3(Cfg::WP, Cfg::T, 1);
+        dim3 block(Cfg::T, Cfg::WP, 1);
         kern<<<grid, block, Cfg::SMEM, s>>>(a, *reinterpret_cast<const CUtensorMap *>(tm.b));
         return cudaGetLastError();
     }

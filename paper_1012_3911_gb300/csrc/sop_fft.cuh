@@ -88,19 +88,6 @@ template <int A, int B> __device__ __forceinline__ double kdot(double a, double 
     return fmar(a, KVal<A>::v, b * KVal<B>::v);
 }
 
-// a * exp(-2 pi i J / 16), 0 <= J < 8 (the only angles the radix-2^k
-// butterflies below need).
-template <int J, typename C> __device__ __forceinline__ C w16(C a) {
-    if constexpr (J == 0) return a;
-    else if constexpr (J == 4) return mul_mi(a);
-    else if constexpr (J == 2) return mk<C>(kmul<K_R2>(a.x + a.y), kmul<K_R2>(a.y - a.x));
-    else if constexpr (J == 6) return mk<C>(kmul<K_R2>(a.y - a.x), -kmul<K_R2>(a.x + a.y));
-    else if constexpr (J == 1) return mk<C>(kdot<K_C1, K_S1>(a.x, a.y), kdot<K_C1, K_S1>(a.y, -a.x));
-    else if constexpr (J == 3) return mk<C>(kdot<K_S1, K_C1>(a.x, a.y), kdot<K_S1, K_C1>(a.y, -a.x));
-    else if constexpr (J == 5) return mk<C>(kdot<K_C1, K_S1>(a.y, -a.x), -kdot<K_S1, K_C1>(a.y, a.x));
-    else return mk<C>(kdot<K_S1, K_C1>(a.y, -a.x), -kdot<K_C1, K_S1>(a.y, a.x));   // J == 7
-}
-
 // Stage twiddles.  FP32 stores z = w - 1 of w = exp(-2 pi i e/n) (formed in
 // FP64, rounded once) and applies x + z x: the same four FMAs as a complex
 // product, but twiddles near 1 -- the ones a smooth field's energy flows
@@ -136,32 +123,52 @@ __host__ __device__ constexpr double cos48(int j) {
 }
 __host__ __device__ constexpr double sin48(int j) { return cos48(j - 12); }
 
-// x * exp(-2 pi i J / 48) with the constant applied as hi + lo in FP32.
-template <int J> __device__ __forceinline__ float2 rot48(float2 x) {
-    constexpr int j = ((J % 48) + 48) % 48;
-    if constexpr (j == 0) return x;
-    else if constexpr (j == 12) return mul_mi(x);
-    else if constexpr (j == 24) return mk<float2>(-x.x, -x.y);
-    else if constexpr (j == 36) return mul_pi(x);
-    else {
-        constexpr double c = cos48(j), s = sin48(j);
-        constexpr float ch = (float)c, cl = (float)(c - (double)ch);
-        constexpr float sh = (float)s, sl = (float)(s - (double)sh);
-        return mk<float2>(fmar(x.x, ch, fmar(x.y, sh, fmar(x.x, cl, x.y * sl))),
-                          fmar(x.y, ch, fmar(-x.x, sh, fmar(x.y, cl, -(x.x * sl)))));
+// Shear coefficients tan(pi j/48) and sin(2 pi j/48), j = 1..11.
+__host__ __device__ constexpr double shear_t48(int j) {
+    const double t[12] = {0.0,
+                          0.065543462815238228564543724879942794922,
+                          0.13165249758739585347152645740971710359,
+                          0.1989123673796580069115976226446762286,
+                          0.26794919243112270647255365849412763306,
+                          0.33945425886337581553711890089328069302,
+                          0.41421356237309504880168872420969807857,
+                          0.49314542603130412392530089399243144889,
+                          0.57735026918962576450914878050195745565,
+                          0.66817863791929891999775768652308076155,
+                          0.76732698797896034292304169200206568034,
+                          0.87697646299275686724868856712992232268};
+    return t[j];
+}
+
+// x * exp(-2 pi i J / 48).  The quarter turns (-i)^q are exact swaps and
+// negations; the remaining angle phi = 2 pi j/48 < pi/2 is applied as three
+// shears, x += t y; y -= s x; x += t y with t = tan(phi/2), s = sin(phi)
+// (3 FMAs).  A shear has determinant 1 whatever its rounded coefficient, so
+// the product is area-preserving exactly: a rounded constant cannot bias the
+// norm to first order (a rounded cos/sin pair would, with a fixed sign, in
+// every transform).
+template <int J, typename C> __device__ __forceinline__ C rot48(C x) {
+    using R = decltype(x.x);
+    constexpr int jj = ((J % 48) + 48) % 48;
+    constexpr int q = jj / 12, j = jj % 12;
+    C y = x;
+    if constexpr (q == 1) y = mul_mi(x);
+    else if constexpr (q == 2) y = mk<C>(-x.x, -x.y);
+    else if constexpr (q == 3) y = mul_pi(x);
+    if constexpr (j == 0) {
+        return y;
+    } else {
+        constexpr R t = R(shear_t48(j));
+        constexpr R sn = R(sin48(j));
+        R a = fmar(t, y.y, y.x);
+        const R b = fmar(-sn, a, y.y);
+        a = fmar(t, b, a);
+        return mk<C>(a, b);
     }
 }
-template <int J> __device__ __forceinline__ double2 rot48(double2 x) {
-    constexpr int j = ((J % 48) + 48) % 48;
-    if constexpr (j == 0) return x;
-    else if constexpr (j == 12) return mul_mi(x);
-    else if constexpr (j == 24) return mk<double2>(-x.x, -x.y);
-    else if constexpr (j == 36) return mul_pi(x);
-    else {
-        constexpr double c = cos48(j), s = sin48(j);
-        return mk<double2>(fmar(x.x, c, x.y * s), fmar(x.y, c, -(x.x * s)));
-    }
-}
+
+// a * exp(-2 pi i J / 16) for the radix-2^k butterflies.
+template <int J, typename C> __device__ __forceinline__ C w16(C a) { return rot48<3 * J>(a); }
 
 // Compile-time loop: f(std::integral_constant<int, I>) for I in [B, E).
 template <int B, int E, typename F> __device__ __forceinline__ void sfor(F &&f) {
