@@ -46,8 +46,11 @@ def parse_args():
     ap.add_argument("--n", type=int, default=2048, help="lattice side")
     ap.add_argument("--fp64-steps", type=int, default=500, help="split steps of the FP64 sample (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=3, help="benchmark steps of the end-to-end leg (0: skip)")
-    ap.add_argument("--cpu-steps", type=int, default=12, help="oracle split steps of the CPU baseline (0: skip)")
+    ap.add_argument("--cpu-steps", type=int, default=200,
+                    help="oracle split steps of the CPU baseline, about 10-30 s on 16 cores (0: skip)")
     ap.add_argument("--ref-split-steps", type=int, default=2, help="oracle split steps per reference step")
+    ap.add_argument("--profile-every", type=int, default=16,
+                    help="time the passes of one split step in this many (per-class roofline)")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
@@ -229,7 +232,7 @@ def main():
     except Exception:
         bus = None
     sampler = ClockSampler(bus)
-    sop.sop_profile_enable(prop.plan, True)
+    sop.sop_profile_enable(prop.plan, args.profile_every)
     sop.sop_profile_read(prop.plan)
     launches0 = sop.sop_launch_counter(prop.plan)
     events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -242,7 +245,7 @@ def main():
     clocks = sampler.stop()
     launches = sop.sop_launch_counter(prop.plan) - launches0
     cls_ms, cls_n = sop.sop_profile_read(prop.plan)
-    sop.sop_profile_enable(prop.plan, False)
+    sop.sop_profile_enable(prop.plan, 0)
     total_ms = sum(a.elapsed_time(b) for a, b in events)
     if dist is not None:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
@@ -261,7 +264,13 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": ncu_traffic(names[dom]), "kernel": names[dom], "peak_source": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
-                "pass_ms_share": {names[i]: cls_ms[i] / max(1e-12, sum(cls_ms)) for i in range(len(cls_ms)) if cls_n[i]}}
+                "profile_every": args.profile_every,
+                "pass_avg_ms": {names[i]: cls_ms[i] / cls_n[i] for i in range(len(cls_ms)) if cls_n[i]},
+                "pass_timed_launches": {names[i]: cls_n[i] for i in range(len(cls_ms)) if cls_n[i]}}
+    # share of the step per class: sampled average x launches per benchmark step
+    per_step = {0: S + 1, 1: S, 4: -(-(S + 1) // 512)}
+    est = {names[c]: cls_ms[c] / cls_n[c] * k for c, k in per_step.items() if cls_n[c]}
+    roofline["pass_ms_share"] = {k: v / sum(est.values()) for k, v in est.items()}
 
     # ---- FP64 sample, same lattice -----------------------------------------
     fp64 = None

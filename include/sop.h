@@ -131,8 +131,14 @@ int sop_norm(sop_plan plan, double *out);
  * Synchronises the plan stream. */
 int sop_energy(sop_plan plan, double *out);
 
-/* Per-pass device timing with CUDA events on the plan stream.  While
- * enabled, sop_step records an event pair around every kernel it launches.
+/* Per-pass device timing with CUDA events on the plan stream.
+ * every = 0 disables it.  every = 1: sop_step records an event pair around
+ * every kernel it launches.  every = k > 1: only the passes of one split
+ * step in k are bracketed (step indices P = k/2 mod k within each sop_step
+ * call, P = 0..n_steps for the real-space passes) together with every
+ * table set-up kernel; the event records then barely perturb the back-to-
+ * back pass launches, and per-class averages stay unbiased samples.
+ * every < 0 is SOP_EINVAL.
  * sop_profile_read synchronises the stream and returns, per pass class,
  * the summed device milliseconds and the launch count since profiling was
  * enabled (arrays of max_classes entries, SOP_PASS_CLASSES at most); it
@@ -140,7 +146,7 @@ int sop_energy(sop_plan plan, double *out);
  * space (last axis) pass, 2 middle-axis transform pass, 3 one-dimensional
  * whole-step kernel, 4 table set-up kernels. */
 #define SOP_PASS_CLASSES 5
-int sop_profile_enable(sop_plan plan, int on);
+int sop_profile_enable(sop_plan plan, int every);
 int sop_profile_read(sop_plan plan, double *ms, int64_t *launches, int max_classes);
 
 /* Total number of kernels this plan has launched since it was created

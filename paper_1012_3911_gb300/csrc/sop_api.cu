@@ -104,7 +104,7 @@ struct sop_plan_s {
     };
     std::vector<MapEntry> maps;     // tensor maps of psi / scratch per strided axis
 
-    bool prof = false;
+    int prof_every = 0;             // 0: off; 1: every kernel; k > 1: the passes of one split step in k
     std::vector<EventPair> events;
     std::vector<cudaEvent_t> event_pool;
     int64_t launches = 0;
@@ -146,20 +146,21 @@ cudaEvent_t take_event(sop_plan p) {
     return e;
 }
 
-// Launch bracket: counts launches and, when profiling, records events.
+// Launch bracket: counts launches and, when profiling and `sampled`, records events.
 struct Bracket {
     sop_plan p;
     int cls;
+    bool on;
     cudaEvent_t a = nullptr;
-    Bracket(sop_plan pp, int c) : p(pp), cls(c) {
-        if (p->prof) {
+    Bracket(sop_plan pp, int c, bool sampled = true) : p(pp), cls(c), on(pp->prof_every != 0 && sampled) {
+        if (on) {
             a = take_event(p);
             cudaEventRecord(a, p->stream);
         }
     }
     void done(int nlaunch = 1) {
         p->launches += nlaunch;
-        if (p->prof) {
+        if (on) {
             cudaEvent_t b = take_event(p);
             cudaEventRecord(b, p->stream);
             p->events.push_back({a, b, cls});
@@ -350,8 +351,15 @@ void base_args(sop_plan p, PassArgs &a, void *psi, int axis) {
     a.pair_comp[1][1] = 2;
 }
 
-int run_pass(sop_plan p, const PassArgs &a, int nc, int cls, const char *what) {
-    Bracket br(p, cls);
+// Whether the passes of split step P (index within one sop_step call) are
+// timed: all of them, or with sampling every k-th one, P = k/2 mod k.
+bool step_sampled(const sop_plan p, int64_t P) {
+    if (p->prof_every <= 1) return true;
+    return P % p->prof_every == p->prof_every / 2;
+}
+
+int run_pass(sop_plan p, const PassArgs &a, int nc, int cls, const char *what, bool sampled = true) {
+    Bracket br(p, cls, sampled);
     int rc = launch_pass(p, a, nc, what);
     if (rc) return rc;
     br.done();
@@ -482,7 +490,7 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
                         a.mix[pr][2 * (2 * i + j) + 1] = M[i][j].imag();
                     }
             }
-            rc = run_pass(p, a, 2, 0, "Dirac real-space pass");
+            rc = run_pass(p, a, 2, 0, "Dirac real-space pass", step_sampled(p, P));
             if (rc) return rc;
             if (P < n) {
                 PassArgs k;
@@ -491,7 +499,7 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
                 k.post = +1;
                 k.op = OP_DT;
                 k.dtab = p->dtab;
-                rc = run_pass(p, k, 2, 1, "Dirac momentum-space pass");
+                rc = run_pass(p, k, 2, 1, "Dirac momentum-space pass", step_sampled(p, P));
                 if (rc) return rc;
             }
         }
@@ -575,7 +583,8 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
             a.op = OP_V;
             a.vtab = p->v_set ? ((P == 0 || P == n) ? p->vhalf : p->vfull) : nullptr;
             for (int ax = 0; ax < nd; ++ax) a.ftab[ax] = frow(P, ax);
-            rc = run_pass(p, a, 1, 0, "real-space pass");
+            const bool smp = step_sampled(p, P);
+            rc = run_pass(p, a, 1, 0, "real-space pass", smp);
             if (rc) return rc;
             if (P == n) break;
             if (nd == 2) {
@@ -585,14 +594,14 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
                 k.post = +1;
                 k.op = OP_T;
                 for (int ax = 0; ax < nd; ++ax) k.ttab[ax] = p->kin[ax];
-                rc = run_pass(p, k, 1, 1, "momentum-space pass");
+                rc = run_pass(p, k, 1, 1, "momentum-space pass", smp);
                 if (rc) return rc;
             } else {
                 PassArgs y;
                 base_args(p, y, p->psi, 1);
                 y.pre = -1;
                 y.op = OP_NONE;
-                rc = run_pass(p, y, 1, 2, "forward middle-axis pass");
+                rc = run_pass(p, y, 1, 2, "forward middle-axis pass", smp);
                 if (rc) return rc;
                 PassArgs k;
                 base_args(p, k, p->psi, 2);
@@ -600,10 +609,10 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
                 k.post = +1;
                 k.op = OP_T;
                 for (int ax = 0; ax < nd; ++ax) k.ttab[ax] = p->kin[ax];
-                rc = run_pass(p, k, 1, 1, "momentum-space pass");
+                rc = run_pass(p, k, 1, 1, "momentum-space pass", smp);
                 if (rc) return rc;
                 y.pre = +1;
-                rc = run_pass(p, y, 1, 2, "inverse middle-axis pass");
+                rc = run_pass(p, y, 1, 2, "inverse middle-axis pass", smp);
                 if (rc) return rc;
             }
         }
@@ -849,9 +858,10 @@ int sop_energy(sop_plan p, double *out) {
     return SOP_OK;
 }
 
-int sop_profile_enable(sop_plan p, int on) {
+int sop_profile_enable(sop_plan p, int every) {
     if (!p) return fail(SOP_EINVAL, "sop_profile_enable: null plan");
-    p->prof = on != 0;
+    if (every < 0) return fail(SOP_EINVAL, "sop_profile_enable: every < 0");
+    p->prof_every = every;
     return SOP_OK;
 }
 

@@ -148,15 +148,29 @@ template <typename Real, int N, int NC, bool CONTIG> struct AsyncCfg {
     static constexpr int WP = CONTIG ? wp_contig() : wp_strided();
     static constexpr int THREADS = T * WP;
     static constexpr int BR = largest_divisor_le(N, 256);   // box extent along the axis
+    // Strided axes interleave the WP pencils of a tile over the lanes of a
+    // warp (pencil w = tid mod WP), so a warp reads whole landing rows of
+    // 16 bytes or more.  LANES threads of one pencil then share a warp, and
+    // the exchange rows get a pitch RPITCH >= USED with RPITCH = SKEW_B
+    // (mod PER), so that the pencils of a warp fall on different banks; the
+    // rule for SKEW_B was checked against a bank model of every access of
+    // the pass (landing read, exchanges, write-back) for all sizes.
+    static constexpr int LANES = CONTIG ? 32 : (WP >= 32 ? 1 : 32 / WP);
+    static constexpr int PER = 128 / CSZ;   // elements per 128-byte bank line
+    static constexpr int SKEW_H = LANES / (2 * NC) > 1 ? LANES / (2 * NC) : 1;
+    static constexpr int SKEW_B = SKEW_H == 1 ? 1 : ((SKEW_H % PER) ? SKEW_H % PER : PER / 2);
+    static constexpr int USED = (N - 1) + ((N - 1) >> G::LR) + 1;   // exchange row length in use
+    static constexpr int RPITCH = CONTIG ? PITCH : USED + ((SKEW_B - USED % PER) % PER + PER) % PER;
     static constexpr size_t al128(size_t x) { return (x + 127) & ~size_t(127); }
-    static constexpr size_t LAND = (size_t)NC * N * WP * CSZ;       // strided: TMA landing layout [c][i][w]
-    static constexpr size_t XCHG = (size_t)WP * NC * PITCH * CSZ;   // padded per-pencil exchange rows
+    static constexpr size_t LAND = (size_t)NC * N * WP * CSZ;        // strided: TMA landing layout [c][i][w]
+    static constexpr size_t XCHG = (size_t)WP * NC * RPITCH * CSZ;   // padded per-pencil exchange rows
     static constexpr size_t BUF = al128(CONTIG ? XCHG : (LAND > XCHG ? LAND : XCHG));
     static constexpr size_t TWZ = al128((size_t)StageTable<C, N, E>::ENTRIES * CSZ + 16);
     static constexpr size_t AXT = al128((size_t)N * CSZ);   // pass-axis table (field row / kinetic row)
     static constexpr size_t OFF_BUF = 128, OFF_TWZ = OFF_BUF + 2 * BUF, OFF_AXT = OFF_TWZ + TWZ;
     static constexpr size_t SMEM = OFF_AXT + AXT;
     static constexpr bool FITS = SMEM <= 227 * 1024 && THREADS <= 1024;
+    static_assert(USED <= PITCH && USED <= RPITCH, "exchange rows must not overlap");
     // CTAs per SM that shared memory allows; the register budget follows.
     static constexpr int minb() {
         int b = (int)((227 * 1024) / (SMEM > 0 ? SMEM : 1));
@@ -187,9 +201,9 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
     C *twz = reinterpret_cast<C *>(smem + Cfg::OFF_TWZ);   // per-stage twiddles
     C *axt = reinterpret_cast<C *>(smem + Cfg::OFF_AXT);   // pass-axis factor table
 
-    const int t = threadIdx.x;   // thread within the pencil
-    const int w = threadIdx.y;   // pencil within the tile
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int t = CONTIG ? (int)threadIdx.x : tid / WP;   // thread within the pencil
+    const int w = CONTIG ? (int)threadIdx.y : tid % WP;   // pencil within the tile
     const int pz = NC == 2 ? (int)blockIdx.z : 0;
     const int64_t stride = CONTIG ? 1 : a.stride;
     const bool op_v = a.op == OP_V, op_t = a.op == OP_T;
@@ -316,9 +330,12 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         const int b = it & 1;
         const int64_t next = tile + gridDim.x;
         const bool has_next = next < ntiles;
-        if (tid == 0) {
-            if (!CONTIG) bulk_wait_read();   // the tile store out of buffer b ^ 1 has read it
-            fence_proxy_async_smem();        // earlier generic accesses to the buffers precede the copies
+        // Prefetch of the next tile into buffer b ^ 1: at once on the contiguous
+        // axis; on strided axes after the first transform, by which time the
+        // tile store out of that buffer (issued at the end of the previous
+        // iteration) has long been read, so no thread waits for it.
+        if (CONTIG && tid == 0) {
+            fence_proxy_async_smem();   // earlier generic accesses to the buffers precede the copies
             if (has_next) issue(next, b ^ 1);
         }
 
@@ -359,7 +376,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
 
         bool ok = mbar_wait_bounded(b ? bar1 : bar0, (it >> 1) & 1, kWaitLimitNs);
         if (!__syncthreads_and(ok)) {
-            give_up(it, true, has_next, false);
+            give_up(it, true, CONTIG && has_next, false);
             return;
         }
 
@@ -371,7 +388,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         Lay lay[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            C *row = bufc + (w * NC + c) * Cfg::PITCH;
+            C *row = bufc + (w * NC + c) * Cfg::RPITCH;
             lay[c].p = row;
             if constexpr (CONTIG) {
 #pragma unroll
@@ -385,6 +402,11 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         __syncthreads();
 
         if (a.pre != 0) fft_dir<C, N, E, NC, true>(v, lay, t, tw, a.pre);
+        if (!CONTIG && tid == 0) {
+            bulk_wait_read();           // the tile store out of buffer b ^ 1 has read it
+            fence_proxy_async_smem();   // earlier generic accesses to the buffers precede the copies
+            if (has_next) issue(next, b ^ 1);
+        }
 
         if constexpr (NC == 1) {
             if (op_v || op_t) {

@@ -185,8 +185,10 @@ def sop_energy(plan: int) -> float:
     return out.value
 
 
-def sop_profile_enable(plan: int, on: bool = True) -> None:
-    _check(load().sop_profile_enable(plan, int(bool(on))))
+def sop_profile_enable(plan: int, every: int = 1) -> None:
+    """every = 0: off; 1: time every kernel; k > 1: time the passes of one
+    split step in k (and every table set-up kernel)."""
+    _check(load().sop_profile_enable(plan, int(every)))
 
 
 def sop_profile_read(plan: int):

@@ -104,6 +104,20 @@ def test_profiling_counts_passes():
     ms, n = sop.sop_profile_read(prop.plan)
     assert n[4] == 1                          # one field-table build per chunk
     assert sop.sop_launch_counter(prop.plan) - before == sum(n)
+    # sampled: passes of split steps P = 2 mod 4 only (real-space P = 0..10)
+    sop.sop_profile_enable(prop.plan, 4)
+    before = sop.sop_launch_counter(prop.plan)
+    prop.step(10, w.dt, np.concatenate([w.field, w.field]))
+    ms, n = sop.sop_profile_read(prop.plan)
+    assert n[0] == 3 and n[1] == 2 and n[4] == 1
+    assert ms[0] > 0 and ms[1] > 0
+    assert sop.sop_launch_counter(prop.plan) - before == 11 + 10 + 1
+    sop.sop_profile_enable(prop.plan, 0)
+    prop.step(5, w.dt, w.field)
+    ms, n = sop.sop_profile_read(prop.plan)
+    assert sum(n) == 0
+    with pytest.raises(sop.SopError):
+        sop.sop_profile_enable(prop.plan, -1)
 
 
 @pytest.mark.parametrize("comps,dims,dt", [(1, (96, 64), 0.05), (1, (24, 16, 32), 0.05), (4, (64, 48), 1e-4)])
