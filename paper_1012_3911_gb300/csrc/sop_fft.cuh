@@ -304,6 +304,53 @@ template <typename C, int LR> struct LayContig {
     __device__ __forceinline__ C ld(int i) const { return p[off(i)]; }
 };
 
+__host__ __device__ constexpr int pad_off(int i, int lr) { return i + (i >> lr); }
+
+// Padded rows admit immediate addressing: when every exchange index of a
+// stage is one per-thread base b(t) plus a compile-time term X, and the pad
+// of the sum splits as pad_off(b + X) = pad_off(b) + pad_off(X) for every
+// thread t, a thread computes one base address per stage and each access
+// is that base plus a constant.  The two checks below prove the split by
+// enumerating all threads at compile time; where they fail the generic
+// per-element address is used.
+template <typename Lay> struct LayFast {
+    static constexpr bool value = false;
+    static constexpr int LR = 0;
+};
+template <typename C, int LR_> struct LayFast<LayContig<C, LR_>> {
+    static constexpr bool value = true;
+    static constexpr int LR = LR_;
+};
+
+// Stage S writes output r of butterfly j = t + T q to ob(j) + r NS; base
+// b(t) = ob(t) when NS <= T, else t.
+template <int N, int E, int S, int LR> constexpr bool write_split_ok() {
+    constexpr StagePlan P = make_plan(N, E);
+    const int R = P.R[S], NS = P.NS[S], T = N / E, Q = E / R;
+    if (!(NS % T == 0 || T % NS == 0)) return false;
+    for (int t = 0; t < T; ++t) {
+        const int b = NS <= T ? (t / NS) * NS * R + t % NS : t;
+        for (int q = 0; q < Q; ++q) {
+            const int j = t + T * q, j0 = T * q;
+            const int ob = (j / NS) * NS * R + j % NS, ob0 = (j0 / NS) * NS * R + j0 % NS;
+            for (int r = 0; r < R; ++r) {
+                const int i = ob + r * NS, X = ob0 + r * NS;
+                if (i - b != X) return false;
+                if (pad_off(i, LR) != pad_off(b, LR) + pad_off(X, LR)) return false;
+            }
+        }
+    }
+    return true;
+}
+// Exchange reads take element t + T m; base t.
+template <int N, int E, int LR> constexpr bool read_split_ok() {
+    const int T = N / E;
+    for (int t = 0; t < T; ++t)
+        for (int m = 0; m < E; ++m)
+            if (pad_off(t + T * m, LR) != pad_off(t, LR) + pad_off(T * m, LR)) return false;
+    return true;
+}
+
 // WP pencils interleaved as rows [i][w] (w fastest, matching the coalesced
 // global layout of a strided axis).  When a row is shorter than 128 bytes,
 // LM+1 rows share a bank line; the row index is XOR-swizzled so the
@@ -391,6 +438,13 @@ __device__ __forceinline__ void fft_stage(C (&v)[E], const Lay &lay, int t, cons
     constexpr int Q = E / R;
     constexpr bool LAST = (S == P.S - 1);
     static_assert(E % R == 0, "radix must divide E");
+    constexpr bool FASTW = !LAST && LayFast<Lay>::value && write_split_ok<N, E, S, LayFast<Lay>::LR>();
+    C *pw = nullptr;
+    if constexpr (FASTW) {
+        const unsigned ut = (unsigned)t;
+        const int b = NS <= T ? (int)((ut / NS) * NS * R + ut % NS) : t;
+        pw = lay.p + Lay::off(b);
+    }
     sfor<0, Q>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         const int j = t + T * q;
@@ -413,6 +467,13 @@ __device__ __forceinline__ void fft_stage(C (&v)[E], const Lay &lay, int t, cons
         if constexpr (LAST) {
 #pragma unroll
             for (int r = 0; r < R; ++r) v[q + r * Q] = x[r];
+        } else if constexpr (FASTW) {
+            constexpr int j0 = T * q;
+            constexpr int ob0 = (j0 / NS) * NS * R + j0 % NS;
+            sfor<0, R>([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                pw[pad_off(ob0 + r * NS, LayFast<Lay>::LR)] = x[r];
+            });
         } else {
             const int k = j % NS;
             const int ob = (j / NS) * NS * R + k;
@@ -438,10 +499,21 @@ __device__ __forceinline__ void fft_forward_from(C (&v)[NC][E], const Lay (&lay)
             StageTw<C, N, E, S + 1> nxt;
             nxt.template load<SMEM>(tab, t);
             __syncthreads();
+            if constexpr (LayFast<Lay>::value && read_split_ok<N, E, LayFast<Lay>::LR>()) {
 #pragma unroll
-            for (int c = 0; c < NC; ++c)
+                for (int c = 0; c < NC; ++c) {
+                    const C *pr = lay[c].p + Lay::off(t);
+                    sfor<0, E>([&](auto mc) {
+                        constexpr int m = decltype(mc)::value;
+                        v[c][m] = pr[pad_off(T * m, LayFast<Lay>::LR)];
+                    });
+                }
+            } else {
 #pragma unroll
-                for (int m = 0; m < E; ++m) v[c][m] = lay[c].ld(t + T * m);
+                for (int c = 0; c < NC; ++c)
+#pragma unroll
+                    for (int m = 0; m < E; ++m) v[c][m] = lay[c].ld(t + T * m);
+            }
             __syncthreads();
             fft_forward_from<C, N, E, NC, S + 1, SMEM>(v, lay, t, tab, nxt);
         }
