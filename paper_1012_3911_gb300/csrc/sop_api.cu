@@ -96,6 +96,8 @@ struct sop_plan_s {
     void *scratch = nullptr;
 
     int *errflag = nullptr;         // device word set by kernels whose bounded waits gave up
+    unsigned long long *tile_ctr = nullptr;   // tile counters of the persistent passes (one per pair)
+    unsigned long long tile_base[2] = {0, 0};   // their values at the start of the next launch
     bool async_passes = true;       // persistent passes with bulk / TMA prefetch
     struct MapEntry {
         void *ptr;
@@ -218,6 +220,7 @@ int plan_free(sop_plan p) {
     dfree(p->pgrid);
     dfree(p->scratch);
     dfree(p->errflag);
+    dfree(p->tile_ctr);
     if (p->host_stage) cudaFreeHost(p->host_stage);
     if (p->host_result) cudaFreeHost(p->host_result);
     if (p->stage_done) cudaEventDestroy(p->stage_done);
@@ -303,6 +306,9 @@ int launch_pass(sop_plan p, const PassArgs &a0, int nc, const char *what) {
     if (p->async_passes) {
         PassArgs a = a0;
         a.errflag = p->errflag;
+        a.tile_ctr = p->tile_ctr;
+        a.tile_base[0] = p->tile_base[0];
+        a.tile_base[1] = p->tile_base[1];
         a.n_comp_total = p->comps;
         TensorMapBytes tm;
         std::memset(&tm, 0, sizeof(tm));
@@ -313,9 +319,18 @@ int launch_pass(sop_plan p, const PassArgs &a0, int nc, const char *what) {
                 if (rc) return rc;
             }
             cudaError_t e;
-            if (p->f64) e = contig ? launch_async_f64_contig(a, nc, tm, p->stream) : launch_async_f64_strided(a, nc, tm, p->stream);
-            else e = contig ? launch_async_f32_contig(a, nc, tm, p->stream) : launch_async_f32_strided(a, nc, tm, p->stream);
-            if (e == cudaSuccess) return SOP_OK;
+            int64_t adv = 0;
+            if (p->f64)
+                e = contig ? launch_async_f64_contig(a, nc, tm, p->stream, &adv)
+                           : launch_async_f64_strided(a, nc, tm, p->stream, &adv);
+            else
+                e = contig ? launch_async_f32_contig(a, nc, tm, p->stream, &adv)
+                           : launch_async_f32_strided(a, nc, tm, p->stream, &adv);
+            if (e == cudaSuccess) {
+                p->tile_base[0] += (unsigned long long)adv;
+                if (nc == 2) p->tile_base[1] += (unsigned long long)adv;
+                return SOP_OK;
+            }
             if (e != cudaErrorInvalidValue) return cuda_fail(e, what);
             cudaGetLastError();   // size without an asynchronous kernel: use the one-shot pass
         }
@@ -373,7 +388,10 @@ int check_errflag(sop_plan p) {
     cudaError_t e = cudaMemcpy(&h, p->errflag, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(error flag)");
     if (h != 0) {
+        // CTAs that gave up left their tile claims unfinished: restart the counters.
         cudaMemset(p->errflag, 0, sizeof(int));
+        cudaMemset(p->tile_ctr, 0, 2 * sizeof(unsigned long long));
+        p->tile_base[0] = p->tile_base[1] = 0;
         return fail(SOP_ETIMEOUT, "a pass kernel gave up waiting for its tile copies (bounded wait)");
     }
     return SOP_OK;
@@ -715,9 +733,11 @@ int sop_plan_create(sop_plan *out, int ndim, const int64_t *dims, const double *
     if (!rc) rc = dalloc(&p->result, 4 * sizeof(double), "result");
     if (!rc) rc = dalloc(&p->pgrid, (size_t)sum_n * sizeof(double), "momenta");
     if (!rc) rc = dalloc(&p->errflag, sizeof(int), "error flag");
+    if (!rc) rc = dalloc(&p->tile_ctr, 2 * sizeof(unsigned long long), "tile counters");
     if (!rc) {
         e = cudaMemsetAsync(p->errflag, 0, sizeof(int), p->stream);
-        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync(error flag)");
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->tile_ctr, 0, 2 * sizeof(unsigned long long), p->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync(error flag, tile counters)");
     }
     if (!rc) {
         p->row_len = sum_n;

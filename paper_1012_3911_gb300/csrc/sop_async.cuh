@@ -105,6 +105,14 @@ __device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, int c0, int
                  "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
                  : "memory");
 }
+// Programmatic dependent launch: the next kernel of the stream may be
+// scheduled once every CTA of this one has signalled (or exited), and
+// griddep_wait() blocks until the preceding kernel has completed and its
+// writes are visible.
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // The shared-memory sources of this thread's committed bulk stores have been read.
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
@@ -197,6 +205,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
     constexpr int E = Cfg::E, T = Cfg::T, WP = Cfg::WP, CSZ = Cfg::CSZ;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);   // 0, 1: tile buffers; 2: axis table
+    int64_t *s_tile = reinterpret_cast<int64_t *>(smem + 32);   // claimed tiles, by iteration parity
     unsigned char *const buf0 = smem + Cfg::OFF_BUF;       // tile buffer b starts at buf0 + b * BUF
     C *twz = reinterpret_cast<C *>(smem + Cfg::OFF_TWZ);   // per-stage twiddles
     C *axt = reinterpret_cast<C *>(smem + Cfg::OFF_AXT);   // pass-axis factor table
@@ -219,8 +228,14 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
     const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]), barx = smem_addr(&bars[2]);
 
     const int64_t ntiles = a.n_tiles;
-    int64_t tile = blockIdx.x;
-    if (tile >= ntiles) return;
+    // The next pass may start its prologue (barriers, twiddle table) on SMs
+    // this grid leaves; it reads psi and its tables only after griddep_wait.
+    griddep_launch_dependents();
+    // Tiles are claimed one at a time (thread 0), so SMs that run ahead take
+    // more of them whatever the placement of the CTAs.
+    auto claim = [&]() -> int64_t {
+        return (int64_t)(atomicAdd(a.tile_ctr + pz, 1ull) - a.tile_base[pz]);
+    };
 
     if (tid == 0) {
         mbar_init(bar0, 1);
@@ -310,13 +325,24 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
     };
 
     const bool has_axt = axsrc != nullptr;
+    // Before this point only the stage twiddles (written when the plan was
+    // made) are read.  psi and the phase tables may come from the kernel
+    // just before this one in the stream.
+    griddep_wait();
     if (tid == 0) {
-        if (has_axt) {
-            mbar_expect_tx(barx, (uint32_t)(N * CSZ));
-            bulk_g2s(smem_addr(axt), axsrc, (uint32_t)(N * CSZ), barx);
+        const int64_t first = claim();
+        s_tile[0] = first;
+        if (first < ntiles) {
+            if (has_axt) {
+                mbar_expect_tx(barx, (uint32_t)(N * CSZ));
+                bulk_g2s(smem_addr(axt), axsrc, (uint32_t)(N * CSZ), barx);
+            }
+            issue(first, 0);
         }
-        issue(tile, 0);
     }
+    __syncthreads();
+    int64_t tile = s_tile[0];
+    if (tile >= ntiles) return;   // nothing claimed, nothing in flight
     if (has_axt) {
         const bool okx = mbar_wait_bounded(barx, 0, kWaitLimitNs);
         if (!__syncthreads_and(okx)) {
@@ -326,18 +352,22 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
     }
     const C *tw = twz;
 
-    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    for (int it = 0; tile < ntiles; ++it) {
         const int b = it & 1;
-        const int64_t next = tile + gridDim.x;
-        const bool has_next = next < ntiles;
-        // Prefetch of the next tile into buffer b ^ 1: at once on the contiguous
-        // axis; on strided axes after the first transform, by which time the
-        // tile store out of that buffer (issued at the end of the previous
-        // iteration) has long been read, so no thread waits for it.
-        if (CONTIG && tid == 0) {
+        // Claim and prefetch of the next tile into buffer b ^ 1: at once on the
+        // contiguous axis; on strided axes after the first transform, by which
+        // time the tile store out of that buffer (issued at the end of the
+        // previous iteration) has long been read, so no thread waits for it.
+        // The claim reaches the other threads through s_tile[(it + 1) & 1].
+        bool has_next = false;   // meaningful in thread 0
+        auto claim_next = [&]() {
+            const int64_t next = claim();
+            s_tile[(it + 1) & 1] = next;
+            has_next = next < ntiles;
             fence_proxy_async_smem();   // earlier generic accesses to the buffers precede the copies
             if (has_next) issue(next, b ^ 1);
-        }
+        };
+        if (CONTIG && tid == 0) claim_next();
 
         // Pencil of this thread.
         int64_t base, coff[NC];
@@ -403,9 +433,8 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
 
         if (a.pre != 0) fft_dir<C, N, E, NC, true>(v, lay, t, tw, a.pre);
         if (!CONTIG && tid == 0) {
-            bulk_wait_read();           // the tile store out of buffer b ^ 1 has read it
-            fence_proxy_async_smem();   // earlier generic accesses to the buffers precede the copies
-            if (has_next) issue(next, b ^ 1);
+            bulk_wait_read();   // the tile store out of buffer b ^ 1 has read it
+            claim_next();
         }
 
         if constexpr (NC == 1) {
@@ -472,7 +501,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
                     for (int m = 0; m < E; ++m) st_stream(q + T * m, v[c][m]);
                 }
             }
-            __syncthreads();   // the tile buffer is free again
+            __syncthreads();   // the tile buffer is free again; s_tile of the next iteration is set
         } else {
             // Back into the landing layout, then one TMA store per box (clipped at
             // the lattice edge, so inactive pencils are never written).
@@ -484,9 +513,10 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
                 for (int m = 0; m < E; ++m) col[(t + T * m) * WP] = v[c][m];
             }
             fence_proxy_async_smem();   // make these writes visible to the bulk copy engine
-            __syncthreads();
+            __syncthreads();            // also: s_tile of the next iteration is set
             if (tid == 0) store_tile(tile, b);
         }
+        tile = s_tile[(it + 1) & 1];
     }
     if (!CONTIG && tid == 0) bulk_wait_all();   // the last stores are complete before the kernel ends
 }
@@ -499,7 +529,7 @@ cudaError_t ensure_smem_attr(const void *kern, int bytes);
 cudaError_t persistent_grid(const void *kern, int threads, size_t smem, int *blocks_per_sm, int *sms);
 
 template <typename Real, int N, int NC, bool CONTIG>
-cudaError_t launch_async_t(const PassArgs &a0, const TensorMapBytes &tm, cudaStream_t s) {
+cudaError_t launch_async_t(const PassArgs &a0, const TensorMapBytes &tm, cudaStream_t s, int64_t *ctr_advance) {
     using Cfg = AsyncCfg<Real, N, NC, CONTIG>;
     if constexpr (!Cfg::FITS) {
         return cudaErrorInvalidValue;
@@ -515,6 +545,7 @@ cudaError_t launch_async_t(const PassArgs &a0, const TensorMapBytes &tm, cudaStr
             const int64_t others = a.n_pencils / n0;
             a.n_tiles = a.n_xgroups * others * (NC == 1 ? a.n_batch : 1);
         }
+        *ctr_advance = 0;
         if (a.n_tiles <= 0) return cudaSuccess;
         auto kern = pass_kernel_async<Real, N, NC, CONTIG>;
         cudaError_t e = ensure_smem_attr(reinterpret_cast<const void *>(kern), (int)Cfg::SMEM);
@@ -522,13 +553,22 @@ cudaError_t launch_async_t(const PassArgs &a0, const TensorMapBytes &tm, cudaStr
         int per_sm = 0, sms = 0;
         e = persistent_grid(reinterpret_cast<const void *>(kern), Cfg::THREADS, Cfg::SMEM, &per_sm, &sms);
         if (e != cudaSuccess) return e;
-        int64_t blocks = (int64_t)per_sm * sms;
+        int64_t blocks = (int64_t)per_sm * sms / (NC == 2 ? 2 : 1);   // both component pairs resident
         if (blocks > a.n_tiles) blocks = a.n_tiles;
         if (blocks < 1) blocks = 1;
-        dim3 grid((unsigned)blocks, 1, NC == 2 ? 2 : 1);
-        dim3 block(Cfg::T, Cfg::WP, 1);
-        kern<<<grid, block, Cfg::SMEM, s>>>(a, *reinterpret_cast<const CUtensorMap *>(tm.b));
-        return cudaGetLastError();
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)blocks, 1, NC == 2 ? 2 : 1);
+        cfg.blockDim = dim3(Cfg::T, Cfg::WP, 1);
+        cfg.dynamicSmemBytes = Cfg::SMEM;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, kern, a, *reinterpret_cast<const CUtensorMap *>(tm.b));
+        if (e == cudaSuccess) *ctr_advance = a.n_tiles + blocks;
+        return e;
     }
 }
 

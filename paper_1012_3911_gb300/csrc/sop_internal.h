@@ -45,6 +45,12 @@ struct PassArgs {
     int pair_comp[2][2];     // component indices of each pair
     // Persistent asynchronous passes (filled by the launcher)
     int *errflag;            // device word; bit 1 set when a bounded wait gave up
+    // Dynamic tile scheduling: CTAs claim tiles with atomicAdd on
+    // tile_ctr[pz] (pz: component pair); claim - tile_base[pz] is the tile
+    // index.  A launch advances each counter it uses by n_tiles + gridDim.x
+    // (every CTA ends with one claim past the last tile).
+    unsigned long long *tile_ctr;
+    unsigned long long tile_base[2];
     int64_t n_tiles;         // tiles of the pass (per component pair for nc == 2)
     int64_t n_xgroups;       // strided: tiles along x
     int64_t o_stride;        // strided: element stride of the remaining coordinate
@@ -75,13 +81,18 @@ cudaError_t launch_pass_f64_contig(const PassArgs &a, int nc, cudaStream_t s);
 cudaError_t launch_pass_f64_strided(const PassArgs &a, int nc, cudaStream_t s);
 // Persistent passes with asynchronous (bulk / TMA) prefetch of the next tile.
 // tmap: the 4D tensor map of psi for strided axes (ignored for axis 0).
+// *ctr_advance: how far the launch moves the tile counters.
 struct TensorMapBytes {
     alignas(64) unsigned char b[128];
 };
-cudaError_t launch_async_f32_contig(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s);
-cudaError_t launch_async_f32_strided(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s);
-cudaError_t launch_async_f64_contig(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s);
-cudaError_t launch_async_f64_strided(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s);
+cudaError_t launch_async_f32_contig(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s,
+                                 int64_t *ctr_advance);
+cudaError_t launch_async_f32_strided(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s,
+                                 int64_t *ctr_advance);
+cudaError_t launch_async_f64_contig(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s,
+                                 int64_t *ctr_advance);
+cudaError_t launch_async_f64_strided(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s,
+                                 int64_t *ctr_advance);
 // Pencils per CTA of the asynchronous pass (the tensor-map box width for strided axes).
 int async_pencils_per_cta(bool f64, int n, int nc, bool contig);
 cudaError_t launch_1d_f32(const Args1D &a, int n, cudaStream_t s);

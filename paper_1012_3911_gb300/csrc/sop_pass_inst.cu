@@ -42,13 +42,14 @@ cudaError_t SOP_LAUNCH_NAME(const PassArgs &a, int nc, cudaStream_t s) {
     }
 }
 
-cudaError_t SOP_ASYNC_NAME(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s) {
+cudaError_t SOP_ASYNC_NAME(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s,
+                           int64_t *ctr_advance) {
     const int n = (int)a.dims[a.axis];
     switch (n) {
 #define SOP_CASE(N)                                                                           \
     case N:                                                                                   \
-        return nc == 1 ? launch_async_t<SOP_REAL, N, 1, (SOP_CONTIG != 0)>(a, tmap, s)        \
-                       : launch_async_t<SOP_REAL, N, 2, (SOP_CONTIG != 0)>(a, tmap, s);
+        return nc == 1 ? launch_async_t<SOP_REAL, N, 1, (SOP_CONTIG != 0)>(a, tmap, s, ctr_advance) \
+                       : launch_async_t<SOP_REAL, N, 2, (SOP_CONTIG != 0)>(a, tmap, s, ctr_advance);
         SOP_SIZES(SOP_CASE)
 #undef SOP_CASE
         default:
