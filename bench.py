@@ -49,7 +49,7 @@ def parse_args():
     ap.add_argument("--cpu-steps", type=int, default=200,
                     help="oracle split steps of the CPU baseline, about 10-30 s on 16 cores (0: skip)")
     ap.add_argument("--ref-split-steps", type=int, default=2, help="oracle split steps per reference step")
-    ap.add_argument("--profile-every", type=int, default=16,
+    ap.add_argument("--profile-every", type=int, default=64,
                     help="time the passes of one split step in this many (per-class roofline)")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()

@@ -258,10 +258,11 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
     // Strided axes: the TMA boxes of tile tl, f(component slot, box, coords...)
     // with coordinates (x [in 8-byte units], axis 1, axis 2, component).
     auto tile_boxes = [&](int64_t tl, auto &&f) {
-        const int64_t bidx = NC == 1 ? tl / tiles_per_batch : 0;
-        const int64_t rem = NC == 1 ? tl - bidx * tiles_per_batch : tl;
-        const int64_t o = rem / a.n_xgroups;
-        const int64_t xg = rem - o * a.n_xgroups;
+        const uint32_t ut = (uint32_t)tl, ng = (uint32_t)a.n_xgroups;
+        const uint32_t bidx = NC == 1 ? ut / (uint32_t)tiles_per_batch : 0u;
+        const uint32_t rem = NC == 1 ? ut - bidx * (uint32_t)tiles_per_batch : ut;
+        const uint32_t o = rem / ng;
+        const uint32_t xg = rem - o * ng;
         const int x0 = (int)(xg * WP) * (CSZ / 8);
         for (int c = 0; c < NC; ++c) {
             const int cc = (int)comp_index(c, bidx);
@@ -329,6 +330,11 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
     // made) are read.  psi and the phase tables may come from the kernel
     // just before this one in the stream.
     griddep_wait();
+    // Thread 0 claims one tile ahead: the claim for the tile after the
+    // current one is made when the current one is issued, so the latency of
+    // the atomic is hidden behind a whole tile.  Claims stop after the first
+    // one past the last tile.
+    int64_t ahead = ntiles;
     if (tid == 0) {
         const int64_t first = claim();
         s_tile[0] = first;
@@ -338,6 +344,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
                 bulk_g2s(smem_addr(axt), axsrc, (uint32_t)(N * CSZ), barx);
             }
             issue(first, 0);
+            ahead = claim();
         }
     }
     __syncthreads();
@@ -361,36 +368,49 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         // The claim reaches the other threads through s_tile[(it + 1) & 1].
         bool has_next = false;   // meaningful in thread 0
         auto claim_next = [&]() {
-            const int64_t next = claim();
+            const int64_t next = ahead;
             s_tile[(it + 1) & 1] = next;
             has_next = next < ntiles;
             fence_proxy_async_smem();   // earlier generic accesses to the buffers precede the copies
-            if (has_next) issue(next, b ^ 1);
+            if (has_next) {
+                issue(next, b ^ 1);
+                ahead = claim();
+            }
         };
         if (CONTIG && tid == 0) claim_next();
 
-        // Pencil of this thread.
+        // Pencil of this thread: first point (linear index base) and lattice
+        // coordinates co (0 along the pass axis).  Pencil and tile counts are
+        // below 2^31, so the index arithmetic runs in 32 bits.
         int64_t base, coff[NC];
+        int co[3] = {0, 0, 0};
         bool active;
         if constexpr (CONTIG) {
-            const int64_t p = tile * WP + w;
-            active = p < total;
-            const int64_t pc = active ? p : 0;
-            int64_t bidx = 0, pp = pc;
+            const uint32_t p = (uint32_t)tile * WP + w;
+            active = p < (uint32_t)total;
+            const uint32_t pc = active ? p : 0u;
+            uint32_t bidx = 0, pp = pc;
             if (NC == 1) {
-                bidx = pc / per_batch;
-                pp = pc - bidx * per_batch;
+                bidx = pc / (uint32_t)per_batch;
+                pp = pc - bidx * (uint32_t)per_batch;
             }
-            base = pp * N;
+            base = (int64_t)pp * N;
+            const uint32_t n1 = (uint32_t)a.dims[1];
+            if (a.ndim >= 2) co[1] = (int)(pp % n1);
+            if (a.ndim == 3) co[2] = (int)(pp / n1);
 #pragma unroll
             for (int c = 0; c < NC; ++c) coff[c] = comp_index(c, bidx) * a.comp_stride;
         } else {
-            const int64_t bidx = NC == 1 ? tile / tiles_per_batch : 0;
-            const int64_t rem = NC == 1 ? tile - bidx * tiles_per_batch : tile;
-            const int64_t o = rem / a.n_xgroups;
-            const int64_t x = (rem - o * a.n_xgroups) * WP + w;
-            active = x < n0;
-            base = (active ? x : 0) + o * a.o_stride;
+            const uint32_t ut = (uint32_t)tile, ng = (uint32_t)a.n_xgroups;
+            const uint32_t bidx = NC == 1 ? ut / (uint32_t)tiles_per_batch : 0u;
+            const uint32_t rem = NC == 1 ? ut - bidx * (uint32_t)tiles_per_batch : ut;
+            const uint32_t o = rem / ng;   // the remaining coordinate (z for axis 1, y for axis 2)
+            const uint32_t x = (rem - o * ng) * WP + w;
+            active = x < (uint32_t)n0;
+            const uint32_t xc = active ? x : 0u;
+            base = (int64_t)xc + (int64_t)o * a.o_stride;
+            co[0] = (int)xc;
+            if (a.ndim == 3) co[a.axis == 1 ? 2 : 1] = (int)o;
 #pragma unroll
             for (int c = 0; c < NC; ++c) coff[c] = comp_index(c, bidx) * a.comp_stride;
         }
@@ -445,8 +465,6 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax)
                     tab[ax] = reinterpret_cast<const C *>(op_v ? a.ftab[ax] : a.ttab[ax]);
-                int co[3];
-                unravel3(base, a.dims, a.ndim, co);
                 C g = Ph::one();
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax)
