@@ -72,6 +72,7 @@ struct sop_plan_s {
     bool v_set = false;
 
     void *tw[3] = {nullptr, nullptr, nullptr};
+    void *stw[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};   // per-stage tables, nc = 1, 2
     void *vhalf = nullptr, *vfull = nullptr;
     void *kin[3] = {nullptr, nullptr, nullptr};
     void *dtab = nullptr;
@@ -206,6 +207,8 @@ int plan_free(sop_plan p) {
     cudaStreamSynchronize(p->stream);
     for (int a = 0; a < 3; ++a) {
         dfree(p->tw[a]);
+        dfree(p->stw[a][0]);
+        dfree(p->stw[a][1]);
         dfree(p->kin[a]);
     }
     dfree(p->V);
@@ -307,6 +310,7 @@ int launch_pass(sop_plan p, const PassArgs &a0, int nc, const char *what) {
         PassArgs a = a0;
         a.errflag = p->errflag;
         a.tile_ctr = p->tile_ctr;
+        a.stw = p->stw[a.axis][nc - 1];
         a.tile_base[0] = p->tile_base[0];
         a.tile_base[1] = p->tile_base[1];
         a.n_comp_total = p->comps;
@@ -758,6 +762,26 @@ int sop_plan_create(sop_plan *out, int ndim, const int64_t *dims, const double *
             return cuda_fail(e, "build_twiddles");
         }
         p->launches++;
+        // per-stage tables of the persistent passes (nc = 2 only for the Dirac pairs)
+        for (int nc = 1; nc <= (components == 4 ? 2 : 1); ++nc) {
+            auto st = p->f64 ? stage_table_f64 : stage_table_f32;
+            const int entries = st((int)dims[a], nc, nullptr, nullptr, p->stream);
+            if (entries < 0) continue;
+            rc = dalloc(&p->stw[a][nc - 1], (size_t)(entries > 0 ? entries : 1) * p->csz, "stage twiddles");
+            if (rc) {
+                plan_free(p);
+                return rc;
+            }
+            if (entries > 0) {
+                st((int)dims[a], nc, p->stw[a][nc - 1], p->tw[a], p->stream);
+                p->launches++;
+            }
+        }
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        plan_free(p);
+        return cuda_fail(e, "stage twiddle tables");
     }
     std::vector<double> pg;
     for (int a = 0; a < ndim; ++a)

@@ -28,6 +28,10 @@
 
 #include "sop_kernels.cuh"
 
+#ifndef SOP_LEAN_TABLES
+#define SOP_LEAN_TABLES 1
+#endif
+
 namespace sop {
 
 // ---------------------------------------------------------------------------
@@ -176,14 +180,24 @@ template <typename Real, int N, int NC, bool CONTIG> struct AsyncCfg {
     static constexpr size_t TWZ = al128((size_t)StageTable<C, N, E>::ENTRIES * CSZ + 16);
     static constexpr size_t AXT = al128((size_t)N * CSZ);   // pass-axis table (field row / kinetic row)
     static constexpr size_t OFF_BUF = 128, OFF_TWZ = OFF_BUF + 2 * BUF, OFF_AXT = OFF_TWZ + TWZ;
-    static constexpr size_t SMEM = OFF_AXT + AXT;
+    // Lean layout: the stage twiddles are read from global memory through L1
+    // instead of shared memory, when that lets one more CTA share the SM.
+    // Used for the complex64 Dirac pair passes on strided axes, which read
+    // no axis table.  (Measured on GB300: for the single-component passes
+    // the extra CTA does not pay for the L1 reads of the axis row and the
+    // twiddles; 2048^2 complex64 split steps took 61.0 instead of 56.2 us.)
+    static constexpr int ctas_for(size_t bytes) { return (int)((228 * 1024) / (bytes + 1024)); }
+    static constexpr bool LEAN = SOP_LEAN_TABLES != 0 && CSZ == 8 && NC == 2 && !CONTIG &&
+                                 ctas_for(OFF_BUF + 2 * BUF) > ctas_for(OFF_AXT + AXT);
+    static constexpr size_t SMEM = LEAN ? OFF_BUF + 2 * BUF : OFF_AXT + AXT;
     static constexpr bool FITS = SMEM <= 227 * 1024 && THREADS <= 1024;
+    static constexpr int TWM = LEAN ? 2 : 1;   // twiddle source of the FFT (see StageTw)
     static_assert(USED <= PITCH && USED <= RPITCH, "exchange rows must not overlap");
     // CTAs per SM that shared memory allows; the register budget follows.
     static constexpr int minb() {
         int b = (int)((227 * 1024) / (SMEM > 0 ? SMEM : 1));
         const int bt = 2048 / THREADS;
-        const int br = 65536 / (THREADS * 104);   // leave ~104 registers per thread
+        const int br = 65536 / (THREADS * (LEAN ? 64 : 104));   // registers per thread to leave
         if (bt < b) b = bt;
         if (br < b) b = br;
         if (b > 8) b = 8;
@@ -243,7 +257,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         mbar_init(barx, 1);
         fence_mbar_init();
     }
-    StageTable<C, N, E>::fill(twz, reinterpret_cast<const C *>(a.tw), tid, Cfg::THREADS);
+    if constexpr (!Cfg::LEAN) StageTable<C, N, E>::fill(twz, reinterpret_cast<const C *>(a.tw), tid, Cfg::THREADS);
     __syncthreads();
 
     const int64_t per_batch = a.n_pencils;
@@ -326,6 +340,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
     };
 
     const bool has_axt = axsrc != nullptr;
+    const bool axt_smem = !Cfg::LEAN && has_axt;   // axis table copied into shared memory
     // Before this point only the stage twiddles (written when the plan was
     // made) are read.  psi and the phase tables may come from the kernel
     // just before this one in the stream.
@@ -339,7 +354,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         const int64_t first = claim();
         s_tile[0] = first;
         if (first < ntiles) {
-            if (has_axt) {
+            if (axt_smem) {
                 mbar_expect_tx(barx, (uint32_t)(N * CSZ));
                 bulk_g2s(smem_addr(axt), axsrc, (uint32_t)(N * CSZ), barx);
             }
@@ -350,14 +365,14 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
     __syncthreads();
     int64_t tile = s_tile[0];
     if (tile >= ntiles) return;   // nothing claimed, nothing in flight
-    if (has_axt) {
+    if (axt_smem) {
         const bool okx = mbar_wait_bounded(barx, 0, kWaitLimitNs);
         if (!__syncthreads_and(okx)) {
             give_up(0, true, false, true);
             return;
         }
     }
-    const C *tw = twz;
+    const C *tw = Cfg::LEAN ? reinterpret_cast<const C *>(a.stw) : twz;
 
     for (int it = 0; tile < ntiles; ++it) {
         const int b = it & 1;
@@ -422,6 +437,9 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
             const C *vt = reinterpret_cast<const C *>(a.vtab) + base;
 #pragma unroll
             for (int m = 0; m < E; ++m) vpre[m] = ld_stream(vt + (t + T * m));
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m) vpre[m] = Ph::one();
         }
 
         bool ok = mbar_wait_bounded(b ? bar1 : bar0, (it >> 1) & 1, kWaitLimitNs);
@@ -451,7 +469,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         }
         __syncthreads();
 
-        if (a.pre != 0) fft_dir<C, N, E, NC, true>(v, lay, t, tw, a.pre);
+        if (a.pre != 0) fft_dir<C, N, E, NC, Cfg::TWM>(v, lay, t, tw, a.pre);
         if (!CONTIG && tid == 0) {
             bulk_wait_read();   // the tile store out of buffer b ^ 1 has read it
             claim_next();
@@ -459,27 +477,66 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
 
         if constexpr (NC == 1) {
             if (op_v || op_t) {
-                // Pencil-constant part from the other axes' tables, per-point part
-                // from the axis table in shared memory (and the phase values).
+                // Pencil-constant part g from the other axes' tables (absent when
+                // none is set), per-point part from the axis table and, for the
+                // real-space factor, the phase values.  The flags are uniform, so
+                // the loop is specialised on them rather than branching per point.
                 const C *tab[3];
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax)
                     tab[ax] = reinterpret_cast<const C *>(op_v ? a.ftab[ax] : a.ttab[ax]);
                 C g = Ph::one();
+                bool g_set = false;
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax)
-                    if (ax < a.ndim && ax != a.axis && tab[ax] != nullptr) g = Ph::combine(g, ldg_c(tab[ax] + co[ax]));
+                    if (ax < a.ndim && ax != a.axis && tab[ax] != nullptr) {
+                        const C x = ldg_c(tab[ax] + co[ax]);
+                        g = g_set ? Ph::combine(g, x) : x;
+                        g_set = true;
+                    }
                 const Real shi = Real(a.scale_hi), slo = Real(a.scale_lo);
+                auto axis_at = [&](int i) -> C { return Cfg::LEAN ? ldg_c(axsrc + i) : axt[i]; };
+                // f = [V phase] [axis factor] [g], then psi <- psi (1 + f) [* 1/N].
+                auto loop = [&](auto hv_c, auto axt_c, auto g_c, auto scale_c) {
+                    constexpr bool HV = decltype(hv_c)::value, AX = decltype(axt_c)::value;
+                    constexpr bool GG = decltype(g_c)::value;
+                    constexpr int SC = decltype(scale_c)::value;   // 0: none, 1: hi only, 2: hi + lo
 #pragma unroll
-                for (int m = 0; m < E; ++m) {
-                    const int i = t + T * m;
-                    C f = g;
-                    if (has_axt) f = Ph::combine(axt[i], f);
-                    if (op_v) {
-                        if (want_v) f = Ph::combine(vpre[m], f);
-                        v[0][m] = Ph::apply(v[0][m], f);
-                    } else {
-                        v[0][m] = scale2(Ph::apply(v[0][m], f), shi, slo);
+                    for (int m = 0; m < E; ++m) {
+                        C f = HV ? vpre[m] : (AX ? axis_at(t + T * m) : (GG ? g : Ph::one()));
+                        if constexpr (HV && AX) f = Ph::combine(axis_at(t + T * m), f);
+                        if constexpr (GG && (HV || AX)) f = Ph::combine(f, g);
+                        C r = Ph::apply(v[0][m], f);
+                        if constexpr (SC == 1) r = mk<C>(r.x * shi, r.y * shi);
+                        if constexpr (SC == 2) r = scale2(r, shi, slo);
+                        v[0][m] = r;
+                    }
+                };
+                using F_ = std::false_type;
+                using T_ = std::true_type;
+                using S0 = std::integral_constant<int, 0>;
+                using S1 = std::integral_constant<int, 1>;
+                using S2 = std::integral_constant<int, 2>;
+                // Specialised: the real-space factor on the contiguous axis and the
+                // kinetic factor (axis row and g) on strided axes, the passes of a
+                // step; any other combination takes the per-point flags.
+                if (CONTIG && op_v && !g_set) {
+                    if (has_axt) loop(T_{}, T_{}, F_{}, S0{});
+                    else loop(T_{}, F_{}, F_{}, S0{});
+                } else if (!CONTIG && op_t && has_axt && g_set) {
+                    if (slo == Real(0)) loop(F_{}, T_{}, T_{}, S1{});
+                    else loop(F_{}, T_{}, T_{}, S2{});
+                } else {
+#pragma unroll
+                    for (int m = 0; m < E; ++m) {
+                        C f = g;
+                        if (has_axt) f = Ph::combine(axis_at(t + T * m), f);
+                        if (op_v) {
+                            f = Ph::combine(vpre[m], f);
+                            v[0][m] = Ph::apply(v[0][m], f);
+                        } else {
+                            v[0][m] = scale2(Ph::apply(v[0][m], f), shi, slo);
+                        }
                     }
                 }
             }
@@ -507,7 +564,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
 
         if (a.post != 0) {
             if (a.pre != 0) __syncthreads();
-            fft_dir<C, N, E, NC, true>(v, lay, t, tw, a.post);
+            fft_dir<C, N, E, NC, Cfg::TWM>(v, lay, t, tw, a.post);
         }
 
         if constexpr (CONTIG) {
@@ -537,6 +594,23 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         tile = s_tile[(it + 1) & 1];
     }
     if (!CONTIG && tid == 0) bulk_wait_all();   // the last stores are complete before the kernel ends
+}
+
+// Per-stage twiddle table of size N in global memory (lean passes), the
+// layout of StageTable; one CTA fills it from the W_n table.
+template <typename Real, int N, int NC>
+__global__ void stage_table_kernel(void *out, const void *tw) {
+    using C = cplx_t<Real>;
+    StageTable<C, N, Geometry<N, NC>::E>::fill(reinterpret_cast<C *>(out), reinterpret_cast<const C *>(tw),
+                                               (int)threadIdx.x, (int)blockDim.x);
+}
+
+// out == nullptr: the number of entries; else fill out (async on s).
+template <typename Real, int N, int NC>
+int stage_table_t(void *out, const void *tw, cudaStream_t s) {
+    constexpr int entries = StageTable<cplx_t<Real>, N, Geometry<N, NC>::E>::ENTRIES;
+    if (out != nullptr && entries > 0) stage_table_kernel<Real, N, NC><<<1, 256, 0, s>>>(out, tw);
+    return entries;
 }
 
 // ---------------------------------------------------------------------------

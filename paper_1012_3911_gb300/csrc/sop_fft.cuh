@@ -378,9 +378,10 @@ template <typename C, int N, int E, int S> struct StageTw {
     static constexpr int NS = (S < P.S) ? P.NS[S] : 1;
     static constexpr int T = N / E;
     C z[R > 1 ? R - 1 : 1];
-    // tab: the full W_n table in global memory, or (SMEM) this size's
-    // per-stage table in shared memory (see StageTable).
-    template <bool SMEM>
+    // Twiddle source TWM: 0 = the full W_n table in global memory; 1 = this
+    // size's per-stage table (see StageTable) in shared memory; 2 = the same
+    // per-stage table in global memory, read through L1.
+    template <int TWM>
     __device__ __forceinline__ void load(const C *__restrict__ tab, int t);
 };
 
@@ -411,15 +412,16 @@ template <typename C, int N, int E> struct StageTable {
 };
 
 template <typename C, int N, int E, int S>
-template <bool SMEM>
+template <int TWM>
 __device__ __forceinline__ void StageTw<C, N, E, S>::load(const C *__restrict__ tab, int t) {
     if constexpr (S > 0 && S < P.S) {
         static_assert(NS % T == 0 || T % NS == 0, "stage twiddles must split");
-        if constexpr (SMEM) {
+        if constexpr (TWM != 0) {
             constexpr int KS = StageTable<C, N, E>::ks(S), OFF = StageTable<C, N, E>::off(S);
             const int k = t % KS;
 #pragma unroll
-            for (int r = 1; r < R; ++r) z[r - 1] = tab[OFF + (r - 1) * KS + k];
+            for (int r = 1; r < R; ++r)
+                z[r - 1] = TWM == 1 ? tab[OFF + (r - 1) * KS + k] : ldg_c(tab + OFF + (r - 1) * KS + k);
         } else {
             const int k = t % NS;
 #pragma unroll
@@ -487,7 +489,7 @@ __device__ __forceinline__ void fft_stage(C (&v)[E], const Lay &lay, int t, cons
 // and out.  Every thread of the CTA must call it (it contains barriers).
 // tw holds the twiddles of stage S; those of stage S+1 are fetched before the
 // exchange barrier.
-template <typename C, int N, int E, int NC, int S, bool SMEM, typename Lay>
+template <typename C, int N, int E, int NC, int S, int SMEM, typename Lay>
 __device__ __forceinline__ void fft_forward_from(C (&v)[NC][E], const Lay (&lay)[NC], int t, const C *__restrict__ tab,
                                                  const StageTw<C, N, E, S> &tw) {
     constexpr StagePlan P = make_plan(N, E);
@@ -520,7 +522,7 @@ __device__ __forceinline__ void fft_forward_from(C (&v)[NC][E], const Lay (&lay)
     }
 }
 
-template <typename C, int N, int E, int NC, bool SMEM = false, typename Lay>
+template <typename C, int N, int E, int NC, int SMEM = 0, typename Lay>
 __device__ __forceinline__ void fft_forward(C (&v)[NC][E], const Lay (&lay)[NC], int t, const C *__restrict__ tab) {
     StageTw<C, N, E, 0> none;
     fft_forward_from<C, N, E, NC, 0, SMEM>(v, lay, t, tab, none);
@@ -534,7 +536,7 @@ template <typename C, int E, int NC> __device__ __forceinline__ void conj_all(C 
 }
 
 // dir < 0: forward DFT; dir > 0: inverse DFT without the 1/n factor.
-template <typename C, int N, int E, int NC, bool SMEM = false, typename Lay>
+template <typename C, int N, int E, int NC, int SMEM = 0, typename Lay>
 __device__ __forceinline__ void fft_dir(C (&v)[NC][E], const Lay (&lay)[NC], int t, const C *__restrict__ tw,
                                         int dir) {
     if (dir > 0) conj_all<C, E, NC>(v);

@@ -31,6 +31,7 @@ struct PassArgs {
     int post;                // transform after the operator
     int op;                  // PassOp
     const void *tw;          // twiddles exp(-2 pi i e / n), e < n, plan dtype
+    const void *stw;         // the per-stage twiddle table of the pass axis (persistent passes)
     // OP_V / OP_DV: per-point phase table (z-form for FP32, factor for FP64), may be null
     const void *vtab;
     // OP_V: per-axis field phase tables of this pass (null = axis has no field)
@@ -93,6 +94,11 @@ cudaError_t launch_async_f64_contig(const PassArgs &a, int nc, const TensorMapBy
                                  int64_t *ctr_advance);
 cudaError_t launch_async_f64_strided(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s,
                                  int64_t *ctr_advance);
+// Per-stage twiddle table of an n-point axis for the persistent passes:
+// out == nullptr returns its entry count, else fills out from tw (async);
+// -1 for a size without persistent passes.
+int stage_table_f32(int n, int nc, void *out, const void *tw, cudaStream_t s);
+int stage_table_f64(int n, int nc, void *out, const void *tw, cudaStream_t s);
 // Pencils per CTA of the asynchronous pass (the tensor-map box width for strided axes).
 int async_pencils_per_cta(bool f64, int n, int nc, bool contig);
 cudaError_t launch_1d_f32(const Args1D &a, int n, cudaStream_t s);

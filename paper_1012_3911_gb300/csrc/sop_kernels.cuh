@@ -26,9 +26,8 @@ template <typename Real> struct Phase;
 template <> struct Phase<float> {
     using C = float2;
     __device__ __forceinline__ static C one() { return mk<C>(0.f, 0.f); }
-    __device__ __forceinline__ static C combine(C a, C b) {   // (1+a)(1+b) - 1
-        const C ab = cmul(a, b);
-        return mk<C>((a.x + b.x) + ab.x, (a.y + b.y) + ab.y);
+    __device__ __forceinline__ static C combine(C a, C b) {   // (1+a)(1+b) - 1 = a + b + ab
+        return mk<C>(fmar(a.x, b.x, fmar(-a.y, b.y, a.x + b.x)), fmar(a.x, b.y, fmar(a.y, b.x, a.y + b.y)));
     }
     __device__ __forceinline__ static C apply(C psi, C z) {
         return mk<C>(fmar(z.x, psi.x, fmar(-z.y, psi.y, psi.x)), fmar(z.x, psi.y, fmar(z.y, psi.x, psi.y)));

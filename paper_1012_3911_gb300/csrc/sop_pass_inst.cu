@@ -57,4 +57,18 @@ cudaError_t SOP_ASYNC_NAME(const PassArgs &a, int nc, const TensorMapBytes &tmap
     }
 }
 
+#if SOP_CONTIG
+int SOP_CAT(stage_table, SOP_CAT(SOP_SUFFIX_, SOP_REAL))(int n, int nc, void *out, const void *tw, cudaStream_t s) {
+    switch (n) {
+#define SOP_CASE(N) \
+    case N:         \
+        return nc == 1 ? stage_table_t<SOP_REAL, N, 1>(out, tw, s) : stage_table_t<SOP_REAL, N, 2>(out, tw, s);
+        SOP_SIZES(SOP_CASE)
+#undef SOP_CASE
+        default:
+            return -1;
+    }
+}
+#endif
+
 }  // namespace sop
