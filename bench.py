@@ -30,6 +30,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1012_3911_gb300 import replicas  # noqa: E402  (no torch import at module load)
+
 METRIC = "grid-pt-steps/s and HBM-roofline % per split step, FP32 vs FP64 at stated err"
 UNIT = "grid-pt-steps/s"
 FALLBACK_HBM_GBS = 6800.0
@@ -48,18 +50,13 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3, help="benchmark steps of the end-to-end leg (0: skip)")
     ap.add_argument("--cpu-steps", type=int, default=200,
                     help="oracle split steps of the CPU baseline, about 10-30 s on 16 cores (0: skip)")
+    ap.add_argument("--cpu-one-core-steps", type=int, default=8,
+                    help="oracle split steps timed on one core beside the all-core baseline (0: skip)")
     ap.add_argument("--ref-split-steps", type=int, default=2, help="oracle split steps per reference step")
     ap.add_argument("--profile-every", type=int, default=64,
                     help="time the passes of one split step in this many (per-class roofline)")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
-
-
-def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
 
 
 def measured_peaks():
@@ -182,7 +179,7 @@ def run_reference(args, rank, world):
 
 def main():
     args = parse_args()
-    rank, world, local = dist_env()
+    rank, world, local = replicas.dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
@@ -246,12 +243,8 @@ def main():
     launches = sop.sop_launch_counter(prop.plan) - launches0
     cls_ms, cls_n = sop.sop_profile_read(prop.plan)
     sop.sop_profile_enable(prop.plan, 0)
-    total_ms = sum(a.elapsed_time(b) for a, b in events)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * w.npoints * S * args.steps / (total_ms * 1e-3)
+    total_ms = replicas.max_over_ranks(sum(a.elapsed_time(b) for a, b in events), dist, "cuda")
+    value = replicas.job_throughput(w.npoints, S, args.steps, world, total_ms)
 
     # ---- roofline of the dominant kernel -----------------------------------
     names = sop.PASS_CLASS_NAMES
@@ -267,6 +260,12 @@ def main():
                 "profile_every": args.profile_every,
                 "pass_avg_ms": {names[i]: cls_ms[i] / cls_n[i] for i in range(len(cls_ms)) if cls_n[i]},
                 "pass_timed_launches": {names[i]: cls_n[i] for i in range(len(cls_ms)) if cls_n[i]}}
+    # whole split step against the byte model: B_min = two psi round trips + FP32 V;
+    # the pass design moves exactly that in 2D (one x pass, one y pass per step)
+    t_split = total_ms / args.steps / S * 1e-3
+    b_min = 2 * 2 * 8 * w.npoints + 4 * w.npoints
+    roofline["step_b_min_bytes"] = b_min
+    roofline["step_b_min_frac"] = b_min / t_split / 1e9 / peak
     # share of the step per class: sampled average x launches per benchmark step
     per_step = {0: S + 1, 1: S, 4: -(-(S + 1) // 512)}
     est = {names[c]: cls_ms[c] / cls_n[c] * k for c, k in per_step.items() if cls_n[c]}
@@ -301,6 +300,8 @@ def main():
         host = torch.from_numpy(w.psi0.astype(np.complex64)).pin_memory()
         src = host.clone()
         ts = []
+        # same per-pass event sampling as the device-timed region, so the two compare
+        sop.sop_profile_enable(prop.plan, args.profile_every)
         for k in range(args.e2e_steps + 1):
             host.copy_(src)
             flush.fill_(1.0)
@@ -310,6 +311,8 @@ def main():
             t1 = time.perf_counter()
             if k > 0:
                 ts.append(t1 - t0)
+        sop.sop_profile_read(prop.plan)
+        sop.sop_profile_enable(prop.plan, 0)
         nbytes = host.numel() * host.element_size()
         e2e = {"value": world * w.npoints * S / (sum(ts) / len(ts)), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
@@ -328,6 +331,15 @@ def main():
         tcpu = time.perf_counter() - t0
         cpu = {"value": w.npoints * nc / tcpu, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{nc} of {S} split steps on the full {args.n}x{args.n} lattice (FP64, {tcpu:.1f} s)"}
+        if args.cpu_one_core_steps > 0:
+            n1 = args.cpu_one_core_steps
+            oracle.set_threads(1)
+            t0 = time.perf_counter()
+            oracle.schrodinger_propagate(w.psi0, w.V, w.spacing, w.dt, n1, w.field[:n1])
+            t1c = time.perf_counter() - t0
+            oracle.set_threads(cores)
+            cpu["one_core"] = {"value": w.npoints * n1 / t1c, "unit": UNIT, "cores": 1,
+                               "sample": f"{n1} split steps, same lattice ({t1c:.1f} s)"}
         err = {"split_steps": nc}
         for dt_name in ("c64", "c128"):
             p = sop.Propagator(w.dims, w.spacing, 1, dt_name)
