@@ -192,6 +192,9 @@ template <typename Real, int N, int NC, bool CONTIG> struct AsyncCfg {
     static constexpr size_t SMEM = LEAN ? OFF_BUF + 2 * BUF : OFF_AXT + AXT;
     static constexpr bool FITS = SMEM <= 227 * 1024 && THREADS <= 1024;
     static constexpr int TWM = LEAN ? 2 : 1;   // twiddle source of the FFT (see StageTw)
+    // On the contiguous axis a pencil is whole warps (threadIdx.y = pencil), so
+    // its exchanges synchronise only its own warps (named barrier 1 + pencil).
+    static constexpr bool PENCIL_BAR = CONTIG && T % 32 == 0 && WP > 1 && WP <= 15;
     static_assert(USED <= PITCH && USED <= RPITCH, "exchange rows must not overlap");
     // CTAs per SM that shared memory allows; the register budget follows.
     static constexpr int minb() {
@@ -451,6 +454,9 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         // Registers <- tile buffer (landing layout), then the buffer becomes
         // the exchange buffer.
         C *bufc = reinterpret_cast<C *>(buf0 + b * Cfg::BUF);
+        using Bar = std::conditional_t<Cfg::PENCIL_BAR, BarGroup, BarCTA>;
+        Bar pbar;
+        if constexpr (Cfg::PENCIL_BAR) pbar = BarGroup{1 + w, T};
         C v[NC][E];
         using Lay = LayContig<C, Cfg::G::LR>;   // exchange rows, one per pencil and component
         Lay lay[NC];
@@ -467,9 +473,9 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
                 for (int m = 0; m < E; ++m) v[c][m] = col[(t + T * m) * WP];
             }
         }
-        __syncthreads();
+        pbar.sync();   // the landing rows become exchange rows
 
-        if (a.pre != 0) fft_dir<C, N, E, NC, Cfg::TWM>(v, lay, t, tw, a.pre);
+        if (a.pre != 0) fft_dir<C, N, E, NC, Cfg::TWM>(v, lay, t, tw, a.pre, pbar);
         if (!CONTIG && tid == 0) {
             bulk_wait_read();   // the tile store out of buffer b ^ 1 has read it
             claim_next();
@@ -563,8 +569,8 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         }
 
         if (a.post != 0) {
-            if (a.pre != 0) __syncthreads();
-            fft_dir<C, N, E, NC, Cfg::TWM>(v, lay, t, tw, a.post);
+            if (a.pre != 0) pbar.sync();
+            fft_dir<C, N, E, NC, Cfg::TWM>(v, lay, t, tw, a.post, pbar);
         }
 
         if constexpr (CONTIG) {

@@ -364,6 +364,16 @@ template <typename C, int WP, int SH, int LM> struct LayStrided {
 
 template <typename C> __device__ __forceinline__ C ldg_c(const C *p) { return __ldg(p); }
 
+// Barrier of the threads that share an exchange buffer: the whole CTA, or
+// (BarGroup) the warps of one pencil, a named barrier of n threads.
+struct BarCTA {
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+struct BarGroup {
+    int id, n;   // barrier 1..15 (0 is __syncthreads), thread count (a multiple of 32)
+    __device__ __forceinline__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+};
+
 // Stage twiddles of one thread.  In stage s (radix R, Ns = product of the
 // earlier radices) butterfly j = t + T q multiplies input r by
 // W_{Ns R}^{(j mod Ns) r}.  Either Ns divides T, and j mod Ns = t mod Ns for
@@ -489,9 +499,9 @@ __device__ __forceinline__ void fft_stage(C (&v)[E], const Lay &lay, int t, cons
 // and out.  Every thread of the CTA must call it (it contains barriers).
 // tw holds the twiddles of stage S; those of stage S+1 are fetched before the
 // exchange barrier.
-template <typename C, int N, int E, int NC, int S, int SMEM, typename Lay>
+template <typename C, int N, int E, int NC, int S, int SMEM, typename Lay, typename Bar>
 __device__ __forceinline__ void fft_forward_from(C (&v)[NC][E], const Lay (&lay)[NC], int t, const C *__restrict__ tab,
-                                                 const StageTw<C, N, E, S> &tw) {
+                                                 const StageTw<C, N, E, S> &tw, const Bar &bar) {
     constexpr StagePlan P = make_plan(N, E);
     if constexpr (S < P.S) {
 #pragma unroll
@@ -500,7 +510,7 @@ __device__ __forceinline__ void fft_forward_from(C (&v)[NC][E], const Lay (&lay)
             constexpr int T = N / E;
             StageTw<C, N, E, S + 1> nxt;
             nxt.template load<SMEM>(tab, t);
-            __syncthreads();
+            bar.sync();
             if constexpr (LayFast<Lay>::value && read_split_ok<N, E, LayFast<Lay>::LR>()) {
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
@@ -516,16 +526,17 @@ __device__ __forceinline__ void fft_forward_from(C (&v)[NC][E], const Lay (&lay)
 #pragma unroll
                     for (int m = 0; m < E; ++m) v[c][m] = lay[c].ld(t + T * m);
             }
-            __syncthreads();
-            fft_forward_from<C, N, E, NC, S + 1, SMEM>(v, lay, t, tab, nxt);
+            bar.sync();
+            fft_forward_from<C, N, E, NC, S + 1, SMEM>(v, lay, t, tab, nxt, bar);
         }
     }
 }
 
-template <typename C, int N, int E, int NC, int SMEM = 0, typename Lay>
-__device__ __forceinline__ void fft_forward(C (&v)[NC][E], const Lay (&lay)[NC], int t, const C *__restrict__ tab) {
+template <typename C, int N, int E, int NC, int SMEM = 0, typename Lay, typename Bar = BarCTA>
+__device__ __forceinline__ void fft_forward(C (&v)[NC][E], const Lay (&lay)[NC], int t, const C *__restrict__ tab,
+                                            const Bar &bar = Bar()) {
     StageTw<C, N, E, 0> none;
-    fft_forward_from<C, N, E, NC, 0, SMEM>(v, lay, t, tab, none);
+    fft_forward_from<C, N, E, NC, 0, SMEM>(v, lay, t, tab, none, bar);
 }
 
 template <typename C, int E, int NC> __device__ __forceinline__ void conj_all(C (&v)[NC][E]) {
@@ -536,11 +547,11 @@ template <typename C, int E, int NC> __device__ __forceinline__ void conj_all(C 
 }
 
 // dir < 0: forward DFT; dir > 0: inverse DFT without the 1/n factor.
-template <typename C, int N, int E, int NC, int SMEM = 0, typename Lay>
+template <typename C, int N, int E, int NC, int SMEM = 0, typename Lay, typename Bar = BarCTA>
 __device__ __forceinline__ void fft_dir(C (&v)[NC][E], const Lay (&lay)[NC], int t, const C *__restrict__ tw,
-                                        int dir) {
+                                        int dir, const Bar &bar = Bar()) {
     if (dir > 0) conj_all<C, E, NC>(v);
-    fft_forward<C, N, E, NC, SMEM>(v, lay, t, tw);
+    fft_forward<C, N, E, NC, SMEM>(v, lay, t, tw, bar);
     if (dir > 0) conj_all<C, E, NC>(v);
 }
 
