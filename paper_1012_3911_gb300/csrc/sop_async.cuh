@@ -28,6 +28,9 @@
 
 #include "sop_kernels.cuh"
 
+#ifndef SOP_SINGLE_BUFFER
+#define SOP_SINGLE_BUFFER 1
+#endif
 #ifndef SOP_LEAN_TABLES
 #define SOP_LEAN_TABLES 1
 #endif
@@ -162,15 +165,17 @@ template <typename Real, int N, int NC, bool CONTIG> struct AsyncCfg {
     static constexpr int BR = largest_divisor_le(N, 256);   // box extent along the axis
     // Strided axes interleave the WP pencils of a tile over the lanes of a
     // warp (pencil w = tid mod WP), so a warp reads whole landing rows of
-    // 16 bytes or more.  LANES threads of one pencil then share a warp, and
-    // the exchange rows get a pitch RPITCH >= USED with RPITCH = SKEW_B
-    // (mod PER), so that the pencils of a warp fall on different banks; the
-    // rule for SKEW_B was checked against a bank model of every access of
-    // the pass (landing read, exchanges, write-back) for all sizes.
+    // 16 bytes or more.  Shared-memory accesses of 8-byte (16-byte) elements
+    // are served per half (quarter) warp, PER lanes per 128-byte wavefront,
+    // which then cover PER / WP threads of each pencil; the exchange rows get
+    // a pitch RPITCH >= USED with RPITCH = SKEW_B = PER / (WP NC) (mod PER), so
+    // that the pencil rows of one wavefront fall on different banks.  The rule
+    // was checked against a bank model of every access of the pass (landing
+    // read, exchanges, write-back) for all sizes.
     static constexpr int LANES = CONTIG ? 32 : (WP >= 32 ? 1 : 32 / WP);
     static constexpr int PER = 128 / CSZ;   // elements per 128-byte bank line
-    static constexpr int SKEW_H = LANES / (2 * NC) > 1 ? LANES / (2 * NC) : 1;
-    static constexpr int SKEW_B = SKEW_H == 1 ? 1 : ((SKEW_H % PER) ? SKEW_H % PER : PER / 2);
+    static constexpr int SKEW_H = PER / (WP * NC) > 1 ? PER / (WP * NC) : 1;
+    static constexpr int SKEW_B = SKEW_H % PER;
     static constexpr int USED = (N - 1) + ((N - 1) >> G::LR) + 1;   // exchange row length in use
     static constexpr int RPITCH = CONTIG ? PITCH : USED + ((SKEW_B - USED % PER) % PER + PER) % PER;
     static constexpr size_t al128(size_t x) { return (x + 127) & ~size_t(127); }
@@ -179,7 +184,16 @@ template <typename Real, int N, int NC, bool CONTIG> struct AsyncCfg {
     static constexpr size_t BUF = al128(CONTIG ? XCHG : (LAND > XCHG ? LAND : XCHG));
     static constexpr size_t TWZ = al128((size_t)StageTable<C, N, E>::ENTRIES * CSZ + 16);
     static constexpr size_t AXT = al128((size_t)N * CSZ);   // pass-axis table (field row / kinetic row)
-    static constexpr size_t OFF_BUF = 128, OFF_TWZ = OFF_BUF + 2 * BUF, OFF_AXT = OFF_TWZ + TWZ;
+    // Strided complex128 passes keep one tile buffer instead of two when that
+    // lets one more CTA share the SM: the next tile is then fetched after the
+    // tile store has read the buffer, and the other CTAs cover the wait.
+    // (Measured on GB300: 2048^2 c128 split steps 1394 -> 1354 us; for
+    // complex64 the second buffer is worth more than the extra CTA.)
+    static constexpr int ctas_smem(size_t bytes) { return (int)((228 * 1024) / (bytes + 1024)); }
+    static constexpr bool SINGLE = SOP_SINGLE_BUFFER != 0 && !CONTIG && CSZ == 16 && NC == 1 &&
+                                   ctas_smem(128 + BUF + TWZ + AXT) > ctas_smem(128 + 2 * BUF + TWZ + AXT);
+    static constexpr int NBUF = SINGLE ? 1 : 2;
+    static constexpr size_t OFF_BUF = 128, OFF_TWZ = OFF_BUF + NBUF * BUF, OFF_AXT = OFF_TWZ + TWZ;
     // Lean layout: the stage twiddles are read from global memory through L1
     // instead of shared memory, when that lets one more CTA share the SM.
     // Used for the complex64 Dirac pair passes on strided axes, which read
@@ -188,8 +202,11 @@ template <typename Real, int N, int NC, bool CONTIG> struct AsyncCfg {
     // twiddles; 2048^2 complex64 split steps took 61.0 instead of 56.2 us.)
     static constexpr int ctas_for(size_t bytes) { return (int)((228 * 1024) / (bytes + 1024)); }
     static constexpr bool LEAN = SOP_LEAN_TABLES != 0 && CSZ == 8 && NC == 2 && !CONTIG &&
-                                 ctas_for(OFF_BUF + 2 * BUF) > ctas_for(OFF_AXT + AXT);
-    static constexpr size_t SMEM = LEAN ? OFF_BUF + 2 * BUF : OFF_AXT + AXT;
+                                 ctas_for(OFF_BUF + NBUF * BUF) > ctas_for(OFF_AXT + AXT);
+    static constexpr size_t SMEM = LEAN ? OFF_BUF + NBUF * BUF : OFF_AXT + AXT;
+    // buffer and mbarrier phase parity of iteration it
+    __device__ __forceinline__ static int buf_of(int it) { return SINGLE ? 0 : (it & 1); }
+    __device__ __forceinline__ static uint32_t par_of(int it) { return SINGLE ? (it & 1) : ((it >> 1) & 1); }
     static constexpr bool FITS = SMEM <= 227 * 1024 && THREADS <= 1024;
     static constexpr int TWM = LEAN ? 2 : 1;   // twiddle source of the FFT (see StageTw)
     // On the contiguous axis a pencil is whole warps (threadIdx.y = pencil), so
@@ -335,9 +352,9 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         if (tid == 0) {
             atomicOr(a.errflag, 1);
             if (!CONTIG) bulk_wait_all();
-            const int b = it & 1;
-            if (cur_pending) mbar_wait_bounded(b ? bar1 : bar0, (it >> 1) & 1, kWaitLimitNs);
-            if (next_issued) mbar_wait_bounded(b ? bar0 : bar1, ((it + 1) >> 1) & 1, kWaitLimitNs);
+            const int b = Cfg::buf_of(it);
+            if (cur_pending) mbar_wait_bounded(b ? bar1 : bar0, Cfg::par_of(it), kWaitLimitNs);
+            if (next_issued) mbar_wait_bounded(b ? bar0 : bar1, Cfg::par_of(it + 1), kWaitLimitNs);
             if (ax_pending) mbar_wait_bounded(barx, 0, kWaitLimitNs);
         }
     };
@@ -378,22 +395,29 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
     const C *tw = Cfg::LEAN ? reinterpret_cast<const C *>(a.stw) : twz;
 
     for (int it = 0; tile < ntiles; ++it) {
-        const int b = it & 1;
+        const int b = Cfg::buf_of(it);
         // Claim and prefetch of the next tile into buffer b ^ 1: at once on the
         // contiguous axis; on strided axes after the first transform, by which
         // time the tile store out of that buffer (issued at the end of the
         // previous iteration) has long been read, so no thread waits for it.
         // The claim reaches the other threads through s_tile[(it + 1) & 1].
         bool has_next = false;   // meaningful in thread 0
-        auto claim_next = [&]() {
-            const int64_t next = ahead;
+        int64_t next = ntiles;
+        auto publish_next = [&]() {
+            next = ahead;
             s_tile[(it + 1) & 1] = next;
             has_next = next < ntiles;
+        };
+        auto issue_next = [&]() {
             fence_proxy_async_smem();   // earlier generic accesses to the buffers precede the copies
             if (has_next) {
-                issue(next, b ^ 1);
+                issue(next, Cfg::buf_of(it + 1));
                 ahead = claim();
             }
+        };
+        auto claim_next = [&]() {
+            publish_next();
+            issue_next();
         };
         if (CONTIG && tid == 0) claim_next();
 
@@ -445,7 +469,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
             for (int m = 0; m < E; ++m) vpre[m] = Ph::one();
         }
 
-        bool ok = mbar_wait_bounded(b ? bar1 : bar0, (it >> 1) & 1, kWaitLimitNs);
+        bool ok = mbar_wait_bounded(b ? bar1 : bar0, Cfg::par_of(it), kWaitLimitNs);
         if (!__syncthreads_and(ok)) {
             give_up(it, true, CONTIG && has_next, false);
             return;
@@ -476,7 +500,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         pbar.sync();   // the landing rows become exchange rows
 
         if (a.pre != 0) fft_dir<C, N, E, NC, Cfg::TWM>(v, lay, t, tw, a.pre, pbar);
-        if (!CONTIG && tid == 0) {
+        if (!CONTIG && !Cfg::SINGLE && tid == 0) {
             bulk_wait_read();   // the tile store out of buffer b ^ 1 has read it
             claim_next();
         }
@@ -594,8 +618,15 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
                 for (int m = 0; m < E; ++m) col[(t + T * m) * WP] = v[c][m];
             }
             fence_proxy_async_smem();   // make these writes visible to the bulk copy engine
+            if (Cfg::SINGLE && tid == 0) publish_next();
             __syncthreads();            // also: s_tile of the next iteration is set
-            if (tid == 0) store_tile(tile, b);
+            if (tid == 0) {
+                store_tile(tile, b);
+                if constexpr (Cfg::SINGLE) {
+                    bulk_wait_read();   // the store has read the only buffer
+                    issue_next();
+                }
+            }
         }
         tile = s_tile[(it + 1) & 1];
     }

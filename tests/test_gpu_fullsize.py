@@ -34,6 +34,18 @@ def test_config4_full_lattice_vs_oracle(dtype):
     assert err < (gc.TOL_F64 if dtype == "c128" else gc.TOL_F32_SHORT), err
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_config3_full_lattice_vs_oracle(dtype):
+    """512^3 (1 GiB of complex64 psi): the streaming 3D passes, element by
+    element against the oracle over two split steps (every pass kind)."""
+    w = wl.config3()
+    ref = gc.run_oracle(w, n_steps=2)
+    out, prop = gc.run_gpu(w, dtype, n_steps=2)
+    err = gc.relerr(out, ref)
+    prop.close()
+    assert err < (gc.TOL_F64 if dtype == "c128" else gc.TOL_F32_SHORT), err
+
+
 def test_config2_full_run_invariants():
     """The benchmarked workload end to end (2048^2, 5000 steps): the FP32 run
     keeps its norm, and the FP64 run reverses to the initial state."""
