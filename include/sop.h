@@ -178,6 +178,30 @@ int64_t sop_launch_counter(sop_plan plan);
 int sop_norm_noalloc(const void *psi_dev, int64_t n_values, int dtype, double scale, double *out_dev,
                      void *cuda_stream);
 
+/* Adjoint gradient of a final-state overlap (a follow-on of the method; the
+ * paper has no adjoint).  With psi_0 the bound state (left unchanged),
+ * psi_{n+1} = U_n psi_0 the split steps of Eqs. 6-8 / 10a-b with field
+ * samples E_n (as sop_step), c = <phi|psi_N> = dV sum conj(phi) psi_N and
+ * J = |c|^2, it returns
+ *   *J,
+ *   grad_field[n ndim + a] = dJ/dE_{n,a}       (host, n_steps x ndim; may be NULL)
+ *   grad_V_dev[j]         = dJ/dV_j           (device, prod(dims) doubles; may be NULL)
+ * from costates lambda_N = phi, lambda_n = U_n^dagger lambda_{n+1} (the step
+ * with -dt):  dc/dE_{n,a} = (-i dt/(2 hbar)) (-q) (<lambda_{n+1}|X_a|psi_{n+1}>
+ * + <lambda_n|X_a|psi_n>),  dc/dV_j = (-i dt/(2 hbar)) dV sum_n w_n
+ * conj(lambda_{n,j}) psi_{n,j} (w = 1 at n = 0, N, else 2),  dJ = 2 Re(conj(c) dc).
+ * Forward states are checkpointed every `every` steps and recomputed per
+ * segment.  phi_dev: device array of the plan's dtype and lattice, 16-byte
+ * aligned.  field may be NULL (all zero).  Schroedinger plans only
+ * (SOP_EUNSUPPORTED otherwise); SOP_ESTATE without a bound state; SOP_EINVAL
+ * for n_steps < 1, every < 1, dt zero or not finite, non-finite samples or
+ * bad pointers.  Allocates its checkpoints (ceil(n_steps/every) + every + 2
+ * states) for the call and a second plan for the -dt steps on first use;
+ * synchronises the plan stream. */
+int sop_adjoint_gradient(sop_plan plan, const void *phi_dev, int64_t n_steps, double dt,
+                         const double *field_samples, int64_t every, double *J, double *grad_field,
+                         double *grad_V_dev);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *sop_last_error(void);
 

@@ -35,6 +35,7 @@ UNITS = [
     ("reduce", "sop_reduce.cu", []),
     ("api", "sop_api.cu", []),
     ("noalloc", "sop_noalloc.cu", []),
+    ("adjoint", "sop_adjoint.cu", []),
 ]
 
 

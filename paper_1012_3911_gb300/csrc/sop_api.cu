@@ -70,6 +70,7 @@ struct sop_plan_s {
     void *psi = nullptr;
     double *V = nullptr;
     bool v_set = false;
+    sop_plan rev = nullptr;         // same lattice, stepped with -dt (costates of sop_adjoint_gradient)
 
     void *tw[3] = {nullptr, nullptr, nullptr};
     void *stw[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};   // per-stage tables, nc = 1, 2
@@ -205,6 +206,7 @@ int upload(sop_plan p, double *dst, const double *src, int64_t n) {
 int plan_free(sop_plan p) {
     if (!p) return SOP_OK;
     cudaStreamSynchronize(p->stream);
+    if (p->rev) plan_free(p->rev);
     for (int a = 0; a < 3; ++a) {
         dfree(p->tw[a]);
         dfree(p->stw[a][0]);
@@ -932,5 +934,158 @@ int sop_profile_read(sop_plan p, double *ms, int64_t *launches, int max_classes)
 }
 
 int64_t sop_launch_counter(sop_plan p) { return p ? p->launches : 0; }
+
+int sop_adjoint_gradient(sop_plan p, const void *phi_dev, int64_t n_steps, double dt, const double *field,
+                         int64_t every, double *J, double *grad_field, double *grad_V_dev) {
+    if (!p) return fail(SOP_EINVAL, "sop_adjoint_gradient: null plan");
+    if (p->comps != 1) return fail(SOP_EUNSUPPORTED, "sop_adjoint_gradient: Schroedinger plans only");
+    if (!p->psi) return fail(SOP_ESTATE, "sop_adjoint_gradient: no state bound (psi_0)");
+    if (!phi_dev || !J) return fail(SOP_EINVAL, "sop_adjoint_gradient: phi or J is NULL");
+    if (n_steps < 1 || every < 1) return fail(SOP_EINVAL, "sop_adjoint_gradient: n_steps and every must be >= 1");
+    if (!std::isfinite(dt) || dt == 0.0) return fail(SOP_EINVAL, "sop_adjoint_gradient: dt must be finite and nonzero");
+    if (reinterpret_cast<uintptr_t>(phi_dev) % 16 != 0)
+        return fail(SOP_EINVAL, "sop_adjoint_gradient: phi must be 16-byte aligned");
+    const int nd = p->ndim;
+    const int64_t N = n_steps;
+    if (field)
+        for (int64_t k = 0; k < N * nd; ++k)
+            if (!std::isfinite(field[k])) return fail(SOP_EINVAL, "sop_adjoint_gradient: non-finite field sample");
+    int rc = SOP_OK;
+    // the costate plan: same lattice and potential, its own tables for -dt
+    if (!p->rev) {
+        sop_plan r = nullptr;
+        rc = sop_plan_create(&r, nd, p->dims, p->h, 1, p->f64 ? SOP_C128 : SOP_C64, &p->prm, p->stream);
+        if (rc) return rc;
+        r->async_passes = p->async_passes;
+        p->rev = r;
+    }
+    if (p->v_set) {
+        rc = sop_set_potential(p->rev, p->V, 1);
+        if (rc) return rc;
+    }
+    const size_t sb = (size_t)p->npts * p->csz;
+    const int64_t K = (N + every - 1) / every;           // checkpoints at 0, every, 2 every, ...
+    const int64_t S = std::min<int64_t>(every, N) + 1;   // states of one recomputed segment
+    char *ck = nullptr, *seg = nullptr, *lam = nullptr;
+    double *sdev = nullptr, *cdev = nullptr, *acc = nullptr, *part = nullptr;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(p->stream);
+        dfree(ck);
+        dfree(seg);
+        dfree(lam);
+        dfree(sdev);
+        dfree(cdev);
+        dfree(acc);
+        dfree(part);
+    };
+    rc = dalloc(&ck, (size_t)K * sb, "adjoint checkpoints");
+    if (!rc) rc = dalloc(&seg, (size_t)S * sb, "adjoint segment");
+    if (!rc) rc = dalloc(&lam, sb, "adjoint costate");
+    if (!rc) rc = dalloc(&sdev, (size_t)(N + 1) * 8 * sizeof(double), "adjoint overlaps");
+    if (!rc) rc = dalloc(&cdev, 8 * sizeof(double), "adjoint target overlap");
+    if (!rc) rc = dalloc(&acc, (size_t)p->npts * 2 * sizeof(double), "adjoint accumulator");
+    if (!rc) rc = dalloc(&part, (size_t)inner_partials() * sizeof(double), "adjoint partials");
+    if (rc) {
+        cleanup();
+        return rc;
+    }
+    void *const psi_user = p->psi;
+    const double dV = p->h[0] * (nd > 1 ? p->h[1] : 1.0) * (nd > 2 ? p->h[2] : 1.0);
+    const double *F = field;
+    std::vector<double> zero((size_t)nd, 0.0);
+    auto frow = [&](int64_t n) -> const double * { return F ? F + n * nd : zero.data(); };
+    auto slot = [&](char *base, int64_t k) -> void * { return base + (size_t)k * sb; };
+    auto copy = [&](void *dst, const void *src) -> int {
+        cudaError_t e = cudaMemcpyAsync(dst, src, sb, cudaMemcpyDeviceToDevice, p->stream);
+        return e == cudaSuccess ? SOP_OK : cuda_fail(e, "cudaMemcpyAsync(adjoint state)");
+    };
+    auto inner = [&](const void *a, const void *b, double *out) -> int {
+        cudaError_t e = launch_inner(a, b, p->f64, nd, p->dims, p->h, dV, part, out, p->stream);
+        p->launches += 2;
+        return e == cudaSuccess ? SOP_OK : cuda_fail(e, "adjoint inner product");
+    };
+    auto accum = [&](const void *a, const void *b, double w) -> int {
+        cudaError_t e = launch_accum(a, b, p->f64, p->npts, w, acc, p->stream);
+        p->launches += 1;
+        return e == cudaSuccess ? SOP_OK : cuda_fail(e, "adjoint accumulation");
+    };
+    auto step_on = [&](sop_plan q, void *state, double h, int64_t n) -> int {
+        q->psi = state;
+        return step_impl(q, 1, h, frow(n));
+    };
+    auto body = [&]() -> int {
+        int r = cudaMemsetAsync(acc, 0, (size_t)p->npts * 2 * sizeof(double), p->stream) == cudaSuccess
+                    ? SOP_OK : cuda_fail(cudaGetLastError(), "cudaMemsetAsync(accumulator)");
+        if (r) return r;
+        // forward sweep: psi_0 .. psi_N, checkpoints every `every` steps
+        void *work = slot(seg, 0);
+        if ((r = copy(work, psi_user))) return r;
+        for (int64_t n = 0; n < N; ++n) {
+            if (n % every == 0 && (r = copy(slot(ck, n / every), work))) return r;
+            if ((r = step_on(p, work, dt, n))) return r;
+        }
+        // c = <phi|psi_N>; s_N = <lambda_N|X|psi_N> with lambda_N = phi
+        if ((r = inner(phi_dev, work, cdev))) return r;
+        if ((r = inner(phi_dev, work, sdev + N * 8))) return r;
+        if ((r = copy(lam, phi_dev))) return r;
+        if ((r = accum(lam, work, 1.0))) return r;
+        // backward sweep, one checkpoint segment at a time
+        for (int64_t s = K - 1; s >= 0; --s) {
+            const int64_t n0 = s * every, n1 = std::min<int64_t>(N, n0 + every);
+            if ((r = copy(slot(seg, 0), slot(ck, s)))) return r;
+            for (int64_t k = 0; k + 1 < n1 - n0; ++k) {   // states n0 .. n1 - 1 (psi_{n1} is not needed again)
+                if ((r = copy(slot(seg, k + 1), slot(seg, k)))) return r;
+                if ((r = step_on(p, slot(seg, k + 1), dt, n0 + k))) return r;
+            }
+            for (int64_t m = n1; m > n0; --m) {
+                // lambda_{m-1} = U_{m-1}^dagger lambda_m: the step with -dt
+                if ((r = step_on(p->rev, lam, -dt, m - 1))) return r;
+                const void *psi_m1 = slot(seg, m - 1 - n0);
+                if ((r = inner(lam, psi_m1, sdev + (m - 1) * 8))) return r;
+                if ((r = accum(lam, psi_m1, m - 1 == 0 ? 1.0 : 2.0))) return r;
+            }
+        }
+        return SOP_OK;
+    };
+    rc = body();
+    p->psi = psi_user;
+    if (p->rev) p->rev->psi = nullptr;
+    if (rc) {
+        cleanup();
+        return rc;
+    }
+    // gradients: k_E = (-i dt / (2 hbar)) (-q), k_V = -i dt / (2 hbar)
+    std::vector<double> sh((size_t)(N + 1) * 8), ch(8);
+    cudaError_t e = cudaMemcpyAsync(sh.data(), sdev, sh.size() * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ch.data(), cdev, 8 * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "adjoint results");
+    }
+    const cd c(ch[0], ch[1]);
+    *J = std::norm(c);
+    const double hbar = p->prm.hbar;
+    const cd kE = cd(0.0, -dt / (2.0 * hbar)) * (-p->prm.charge);
+    const cd kV = cd(0.0, -dt / (2.0 * hbar));
+    if (grad_field)
+        for (int64_t n = 0; n < N; ++n)
+            for (int a = 0; a < nd; ++a) {
+                const cd s1(sh[(n + 1) * 8 + 2 + 2 * a], sh[(n + 1) * 8 + 3 + 2 * a]);
+                const cd s0(sh[n * 8 + 2 + 2 * a], sh[n * 8 + 3 + 2 * a]);
+                grad_field[n * nd + a] = 2.0 * std::real(std::conj(c) * kE * (s1 + s0));
+            }
+    if (grad_V_dev) {
+        const cd z = std::conj(c) * kV * dV;
+        e = launch_grad_v(acc, p->npts, z.real(), z.imag(), grad_V_dev, p->stream);
+        p->launches += 1;
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_fail(e, "adjoint potential gradient");
+        }
+    }
+    cleanup();
+    return check_errflag(p);
+}
 
 }  // extern "C"

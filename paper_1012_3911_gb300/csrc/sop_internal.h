@@ -94,6 +94,18 @@ cudaError_t launch_async_f64_contig(const PassArgs &a, int nc, const TensorMapBy
                                  int64_t *ctr_advance);
 cudaError_t launch_async_f64_strided(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s,
                                  int64_t *ctr_advance);
+// Adjoint-gradient reductions (sop_adjoint.cu).  launch_inner writes 8
+// doubles to out: dV (<a|b>, <a|X_0|b>, <a|X_1|b>, <a|X_2|b>) as re, im
+// pairs (axes beyond ndim are zero); partial holds inner_partials() doubles.
+int inner_partials();
+cudaError_t launch_inner(const void *a, const void *b, bool f64, int ndim, const int64_t *dims, const double *h,
+                         double dV, double *partial, double *out, cudaStream_t s);
+// acc[2j], acc[2j+1] += w conj(a_j) b_j
+cudaError_t launch_accum(const void *a, const void *b, bool f64, int64_t npts, double w, double *acc,
+                         cudaStream_t s);
+// g_j = 2 Re((zr + i zi) (acc[2j] + i acc[2j+1]))
+cudaError_t launch_grad_v(const double *acc, int64_t npts, double zr, double zi, double *g, cudaStream_t s);
+
 // Per-stage twiddle table of an n-point axis for the persistent passes:
 // out == nullptr returns its entry count, else fills out from tw (async);
 // -1 for a size without persistent passes.

@@ -217,6 +217,30 @@ def sop_norm_noalloc(psi, n_values: int, dtype: int, scale: float, out, stream=N
     _check(fn(ptr, int(n_values), int(dtype), float(scale), optr, _stream_handle(stream)))
 
 
+def sop_adjoint_gradient(plan: int, phi, n_steps: int, dt: float, field, every: int, ndim: int,
+                         grad_V=None):
+    """J, dJ/dfield (numpy, n_steps x ndim) and, into the CUDA float64 tensor
+    grad_V (one value per lattice point) when given, dJ/dV; see include/sop.h."""
+    lib = load()
+    fn = lib.sop_adjoint_gradient
+    vp, i64, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+    fn.argtypes = [vp, vp, i64, d, vp, i64, ctypes.POINTER(d), vp, vp]
+    fn.restype = ctypes.c_int
+    if not phi.is_cuda or not phi.is_contiguous():
+        raise ValueError("phi must be a contiguous CUDA tensor")
+    keep, fptr = (None, None) if field is None else _field_ptr(field, n_steps, ndim)
+    g = np.zeros((int(n_steps), ndim), dtype=np.float64)
+    J = d()
+    gv = None
+    if grad_V is not None:
+        if not grad_V.is_cuda or not grad_V.is_contiguous():
+            raise ValueError("grad_V must be a contiguous CUDA tensor")
+        gv = grad_V.data_ptr()
+    _check(fn(plan, phi.data_ptr(), int(n_steps), float(dt), fptr, int(every), ctypes.byref(J), g.ctypes.data, gv))
+    del keep
+    return J.value, g
+
+
 class Propagator:
     """A plan plus its bound torch state.
 
@@ -265,6 +289,13 @@ class Propagator:
 
     def energy(self) -> float:
         return sop_energy(self.plan)
+
+    def adjoint_gradient(self, phi, n_steps: int, dt: float, field=None, every: int = 20, grad_V=None):
+        """J = |<phi|psi_N>|^2 from the current state, dJ/dfield and (into
+        grad_V) dJ/dV; the state is left unchanged."""
+        import torch
+        phi_t = torch.as_tensor(phi).to(self.state.device, self.state.dtype).contiguous()
+        return sop_adjoint_gradient(self.plan, phi_t, n_steps, dt, field, every, self.ndim, grad_V)
 
     def close(self) -> None:
         if getattr(self, "plan", None):

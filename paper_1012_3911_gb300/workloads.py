@@ -251,4 +251,36 @@ def config4(n: int = 1024, L: float = 8.0, dt: float = 1e-4, n_steps: int = 1000
                     dt, n_steps, field, meta=dict(A0=A0, omega=omega, T=T, L=L, p0=list(p0)))
 
 
+CONFIG5_SIDES = (256, 384, 512, 768, 1024, 1536, 2048)
+
+
+def config5_instance(k: int, seed: int = 1005, n_steps: int = 400, dt: float = 0.05, h: float = 0.2,
+                     sides=None) -> Workload:
+    """Instance k of the batched + adjoint workload: 2D Schroedinger, sides
+    n_x, n_y drawn independently from 256 ... 2048 (radix 2 and 3), spacing
+    0.2, soft-core V = -1/sqrt(r^2 + 1), field along x with 400 samples
+    E_k ~ N(0, 0.02^2), dt = 0.05, Gaussian psi_0 (sigma = 2) and a Gaussian
+    target phi (sigma = 2, p = 0) at independent offsets in [-5, 5]^2
+    (meta['phi']).  `sides` overrides the drawn (n_x, n_y)."""
+    rng = np.random.default_rng([seed, k])
+    nx, ny = (int(rng.choice(CONFIG5_SIDES)), int(rng.choice(CONFIG5_SIDES)))
+    if sides is not None:
+        nx, ny = sides
+    dims = (nx, ny)
+    sp = (h, h)
+    off = rng.uniform(-5.0, 5.0, size=2)
+    offt = rng.uniform(-5.0, 5.0, size=2)
+    ex = rng.normal(0.0, 0.02, size=n_steps)
+    field = np.stack([ex, np.zeros_like(ex)], axis=1)
+    psi0 = gaussian(dims, sp, tuple(off), 2.0)
+    phi = gaussian(dims, sp, tuple(offt), 2.0)
+    return Workload(f"5_batch_{k}", dims, sp, 1, psi0, soft_core(dims, sp, 1.0), dt, n_steps, field,
+                    meta=dict(phi=phi, offset=list(off), target_offset=list(offt), sides=[nx, ny]))
+
+
+def config5(n_instances: int = 64, seed: int = 1005, n_steps: int = 400):
+    """The 64 instances of the batched + adjoint workload."""
+    return [config5_instance(k, seed, n_steps) for k in range(n_instances)]
+
+
 CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4}
