@@ -192,8 +192,8 @@ int sop_norm_noalloc(const void *psi_dev, int64_t n_values, int dtype, double sc
  * conj(lambda_{n,j}) psi_{n,j} (w = 1 at n = 0, N, else 2),  dJ = 2 Re(conj(c) dc).
  * Forward states are checkpointed every `every` steps and recomputed per
  * segment.  phi_dev: device array of the plan's dtype and lattice, 16-byte
- * aligned.  field may be NULL (all zero).  Schroedinger plans only
- * (SOP_EUNSUPPORTED otherwise); SOP_ESTATE without a bound state; SOP_EINVAL
+ * aligned.  field may be NULL (all zero).  Schroedinger plans with fewer
+ * than 2^31 lattice points only (SOP_EUNSUPPORTED otherwise); SOP_ESTATE without a bound state; SOP_EINVAL
  * for n_steps < 1, every < 1, dt zero or not finite, non-finite samples or
  * bad pointers.  Allocates its checkpoints (ceil(n_steps/every) + every + 2
  * states) for the call and a second plan for the -dt steps on first use;

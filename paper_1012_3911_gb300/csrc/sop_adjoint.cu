@@ -45,12 +45,15 @@ __global__ void __launch_bounds__(kThreads) k_inner(const C *a, const C *b, int6
         const double im = (double)u.x * (double)v.y - (double)u.y * (double)v.x;
         acc[0] += re;
         acc[1] += im;
-        int64_t r = j;
+        // lattice index per axis, in 32 bits (sop_adjoint_gradient accepts
+        // lattices of fewer than 2^31 points)
+        uint32_t r = (uint32_t)j;
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
             if (ax < g.ndim) {
-                const int64_t i = r % g.dims[ax];
-                r /= g.dims[ax];
+                const uint32_t n = (uint32_t)g.dims[ax];
+                const uint32_t i = r % n;
+                r /= n;
                 const double x = g.x0[ax] + (double)i * g.h[ax];
                 acc[2 + 2 * ax] = fma(x, re, acc[2 + 2 * ax]);
                 acc[3 + 2 * ax] = fma(x, im, acc[3 + 2 * ax]);

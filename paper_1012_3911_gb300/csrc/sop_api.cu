@@ -47,6 +47,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr int64_t kFieldChunk = 512;   // real-space indices per field-table chunk
+constexpr int kStageSlots = 8;         // pinned upload slots in flight
 
 struct EventPair {
     cudaEvent_t a, b;
@@ -87,9 +88,12 @@ struct sop_plan_s {
     int64_t foff[3] = {0, 0, 0};
     double *fvec = nullptr;         // device field vectors, (n+1) x ndim
     int64_t fvec_cap = 0;
-    double *host_stage = nullptr;   // pinned staging buffer
+    // pinned staging ring for host -> device uploads: kStageSlots slots of
+    // host_stage_cap doubles; a slot is reused once its previous copy is done
+    double *host_stage = nullptr;
     int64_t host_stage_cap = 0;
-    cudaEvent_t stage_done = nullptr;
+    cudaEvent_t stage_done[kStageSlots] = {};
+    int stage_next = 0, stage_cur = 0;
 
     double *partial = nullptr;
     double *result = nullptr;
@@ -172,34 +176,40 @@ struct Bracket {
     }
 };
 
-int ensure_stage(sop_plan p, int64_t doubles) {
-    if (p->host_stage_cap >= doubles) {
-        // the previous upload must have left the staging buffer
-        cudaError_t e = cudaEventSynchronize(p->stage_done);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
-        return SOP_OK;
+// A free staging slot of at least `doubles` entries; returns its address.
+int ensure_stage(sop_plan p, int64_t doubles, double **slot_out) {
+    if (p->host_stage_cap < doubles) {
+        if (p->host_stage) {
+            for (int k = 0; k < kStageSlots; ++k) cudaEventSynchronize(p->stage_done[k]);
+            cudaFreeHost(p->host_stage);
+            p->host_stage = nullptr;
+            p->host_stage_cap = 0;
+        }
+        const int64_t cap = doubles < 4096 ? 4096 : doubles;
+        cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&p->host_stage),
+                                      (size_t)cap * kStageSlots * sizeof(double), cudaHostAllocDefault);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaHostAlloc");
+        p->host_stage_cap = cap;
     }
-    if (p->host_stage) {
-        cudaEventSynchronize(p->stage_done);
-        cudaFreeHost(p->host_stage);
-        p->host_stage = nullptr;
-    }
-    int64_t cap = doubles < 4096 ? 4096 : doubles;
-    cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&p->host_stage), (size_t)cap * sizeof(double),
-                                  cudaHostAllocDefault);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaHostAlloc");
-    p->host_stage_cap = cap;
+    const int k = p->stage_next;
+    p->stage_next = (k + 1) % kStageSlots;
+    // the copy that last read this slot (kStageSlots uploads ago) has finished
+    cudaError_t e = cudaEventSynchronize(p->stage_done[k]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    *slot_out = p->host_stage + (size_t)k * p->host_stage_cap;
+    p->stage_cur = k;
     return SOP_OK;
 }
 
-// Upload n doubles through the pinned staging buffer to dst (async).
+// Upload n doubles through the pinned staging ring to dst (async).
 int upload(sop_plan p, double *dst, const double *src, int64_t n) {
-    int rc = ensure_stage(p, n);
+    double *slot = nullptr;
+    int rc = ensure_stage(p, n, &slot);
     if (rc) return rc;
-    std::memcpy(p->host_stage, src, (size_t)n * sizeof(double));
-    cudaError_t e = cudaMemcpyAsync(dst, p->host_stage, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, p->stream);
+    std::memcpy(slot, src, (size_t)n * sizeof(double));
+    cudaError_t e = cudaMemcpyAsync(dst, slot, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(upload)");
-    cudaEventRecord(p->stage_done, p->stream);
+    cudaEventRecord(p->stage_done[p->stage_cur], p->stream);
     return SOP_OK;
 }
 
@@ -228,7 +238,8 @@ int plan_free(sop_plan p) {
     dfree(p->tile_ctr);
     if (p->host_stage) cudaFreeHost(p->host_stage);
     if (p->host_result) cudaFreeHost(p->host_result);
-    if (p->stage_done) cudaEventDestroy(p->stage_done);
+    for (int k = 0; k < kStageSlots; ++k)
+        if (p->stage_done[k]) cudaEventDestroy(p->stage_done[k]);
     for (auto &ep : p->events) {
         cudaEventDestroy(ep.a);
         cudaEventDestroy(ep.b);
@@ -724,7 +735,8 @@ int sop_plan_create(sop_plan *out, int ndim, const int64_t *dims, const double *
     int rc = SOP_OK;
     int64_t sum_n = 0;
     for (int a = 0; a < ndim; ++a) sum_n += dims[a];
-    e = cudaEventCreateWithFlags(&p->stage_done, cudaEventDisableTiming);
+    for (int k = 0; k < kStageSlots && e == cudaSuccess; ++k)
+        e = cudaEventCreateWithFlags(&p->stage_done[k], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         plan_free(p);
         return cuda_fail(e, "cudaEventCreate");
@@ -945,6 +957,8 @@ int sop_adjoint_gradient(sop_plan p, const void *phi_dev, int64_t n_steps, doubl
     if (!std::isfinite(dt) || dt == 0.0) return fail(SOP_EINVAL, "sop_adjoint_gradient: dt must be finite and nonzero");
     if (reinterpret_cast<uintptr_t>(phi_dev) % 16 != 0)
         return fail(SOP_EINVAL, "sop_adjoint_gradient: phi must be 16-byte aligned");
+    if (p->npts >= ((int64_t)1 << 31))
+        return fail(SOP_EUNSUPPORTED, "sop_adjoint_gradient: lattices of 2^31 points or more");
     const int nd = p->ndim;
     const int64_t N = n_steps;
     if (field)
@@ -1009,20 +1023,22 @@ int sop_adjoint_gradient(sop_plan p, const void *phi_dev, int64_t n_steps, doubl
         p->launches += 1;
         return e == cudaSuccess ? SOP_OK : cuda_fail(e, "adjoint accumulation");
     };
-    auto step_on = [&](sop_plan q, void *state, double h, int64_t n) -> int {
+    auto step_on = [&](sop_plan q, void *state, double h, int64_t n, int64_t count = 1) -> int {
         q->psi = state;
-        return step_impl(q, 1, h, frow(n));
+        return step_impl(q, count, h, F ? frow(n) : nullptr);
     };
     auto body = [&]() -> int {
         int r = cudaMemsetAsync(acc, 0, (size_t)p->npts * 2 * sizeof(double), p->stream) == cudaSuccess
                     ? SOP_OK : cuda_fail(cudaGetLastError(), "cudaMemsetAsync(accumulator)");
         if (r) return r;
-        // forward sweep: psi_0 .. psi_N, checkpoints every `every` steps
+        // forward sweep to psi_N, checkpoints every `every` steps (a segment is
+        // one sop_step call, with its half steps merged)
         void *work = slot(seg, 0);
         if ((r = copy(work, psi_user))) return r;
-        for (int64_t n = 0; n < N; ++n) {
-            if (n % every == 0 && (r = copy(slot(ck, n / every), work))) return r;
-            if ((r = step_on(p, work, dt, n))) return r;
+        for (int64_t s = 0; s < K; ++s) {
+            const int64_t n0 = s * every, n1 = std::min<int64_t>(N, n0 + every);
+            if ((r = copy(slot(ck, s), work))) return r;
+            if ((r = step_on(p, work, dt, n0, n1 - n0))) return r;
         }
         // c = <phi|psi_N>; s_N = <lambda_N|X|psi_N> with lambda_N = phi
         if ((r = inner(phi_dev, work, cdev))) return r;
