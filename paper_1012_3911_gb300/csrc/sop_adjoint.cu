@@ -33,65 +33,90 @@ struct InnerGeom {
     double x0[3], h[3];   // x_{a,i} = x0[a] + i h[a]
 };
 
+// Products and coordinates are formed in the precision of the state (FP32
+// for complex64); each thread sums kChunk points in that precision and adds
+// the chunk sums in FP64 (FP64 arithmetic is a small fraction of the FP32
+// rate on GB300, and a 16-term FP32 sum errs by ~1e-6 relative).
+constexpr int kChunk = 16;
+
 template <typename C>
 __global__ void __launch_bounds__(kThreads) k_inner(const C *a, const C *b, int64_t npts, InnerGeom g, double *partial) {
+    using R = decltype(C{}.x);
     double acc[kVals];
 #pragma unroll
     for (int k = 0; k < kVals; ++k) acc[k] = 0.0;
-    for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < npts; j += (int64_t)gridDim.x * kThreads) {
-        const C u = a[j], v = b[j];
-        // conj(u) v
-        const double re = (double)u.x * (double)v.x + (double)u.y * (double)v.y;
-        const double im = (double)u.x * (double)v.y - (double)u.y * (double)v.x;
-        acc[0] += re;
-        acc[1] += im;
-        // lattice index per axis, in 32 bits (sop_adjoint_gradient accepts
-        // lattices of fewer than 2^31 points)
-        uint32_t r = (uint32_t)j;
+    R x0[3], hh[3];
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-            if (ax < g.ndim) {
-                const uint32_t n = (uint32_t)g.dims[ax];
-                const uint32_t i = r % n;
-                r /= n;
-                const double x = g.x0[ax] + (double)i * g.h[ax];
-                acc[2 + 2 * ax] = fma(x, re, acc[2 + 2 * ax]);
-                acc[3 + 2 * ax] = fma(x, im, acc[3 + 2 * ax]);
+    for (int ax = 0; ax < 3; ++ax) {
+        x0[ax] = (R)g.x0[ax];
+        hh[ax] = (R)g.h[ax];
+    }
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    while (j < npts) {
+        R loc[kVals];
+#pragma unroll
+        for (int k = 0; k < kVals; ++k) loc[k] = R(0);
+        for (int q = 0; q < kChunk && j < npts; ++q, j += stride) {
+            const C u = a[j], v = b[j];
+            const R re = u.x * v.x + u.y * v.y;   // conj(u) v
+            const R im = u.x * v.y - u.y * v.x;
+            loc[0] += re;
+            loc[1] += im;
+            // lattice index per axis, in 32 bits (sop_adjoint_gradient accepts
+            // lattices of fewer than 2^31 points)
+            uint32_t r = (uint32_t)j;
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                if (ax < g.ndim) {
+                    const uint32_t n = (uint32_t)g.dims[ax];
+                    const uint32_t i = r % n;
+                    r /= n;
+                    const R x = x0[ax] + (R)i * hh[ax];
+                    loc[2 + 2 * ax] += x * re;
+                    loc[3 + 2 * ax] += x * im;
+                }
             }
         }
+#pragma unroll
+        for (int k = 0; k < kVals; ++k) acc[k] += (double)loc[k];
     }
     __shared__ double ws[kVals][kThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < kVals; ++k) {
-        const double s = warp_sum(acc[k]);
-        if (lane == 0) ws[k][wid] = s;
+        const double sum = warp_sum(acc[k]);
+        if (lane == 0) ws[k][wid] = sum;
     }
     __syncthreads();
     if (threadIdx.x < kVals) {
-        double s = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) s += ws[threadIdx.x][w];
-        partial[(int64_t)blockIdx.x * kVals + threadIdx.x] = s;
+        double sum = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) sum += ws[threadIdx.x][w];
+        partial[(int64_t)blockIdx.x * kVals + threadIdx.x] = sum;
     }
 }
 
-// out[k] = scale * sum over blocks, fixed order.
+// out[k] = scale * sum over blocks: warp k sums value k (fixed order).
 __global__ void k_inner_final(const double *partial, int nb, double scale, double *out) {
-    const int k = threadIdx.x;
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (k < kVals) {
-        double s = 0.0;
-        for (int i = 0; i < nb; ++i) s += partial[(int64_t)i * kVals + k];
-        out[k] = scale * s;
+        double sum = 0.0;
+        for (int i = lane; i < nb; i += 32) sum += partial[(int64_t)i * kVals + k];
+        sum = warp_sum(sum);
+        if (lane == 0) out[k] = scale * sum;
     }
 }
 
+// acc_j += w conj(a_j) b_j: the product in the state's precision, the sum in FP64.
 template <typename C>
 __global__ void __launch_bounds__(kThreads) k_accum(const C *a, const C *b, int64_t npts, double w, double2 *acc) {
+    using R = decltype(C{}.x);
+    const R wr = (R)w;
     for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < npts; j += (int64_t)gridDim.x * kThreads) {
         const C u = a[j], v = b[j];
         double2 s = acc[j];
-        s.x = fma(w, (double)u.x * (double)v.x + (double)u.y * (double)v.y, s.x);
-        s.y = fma(w, (double)u.x * (double)v.y - (double)u.y * (double)v.x, s.y);
+        s.x += (double)(wr * (u.x * v.x + u.y * v.y));
+        s.y += (double)(wr * (u.x * v.y - u.y * v.x));
         acc[j] = s;
     }
 }
@@ -125,7 +150,7 @@ cudaError_t launch_inner(const void *a, const void *b, bool f64, int ndim, const
     else
         k_inner<float2><<<kBlocks, kThreads, 0, s>>>(static_cast<const float2 *>(a), static_cast<const float2 *>(b),
                                                        npts, g, partial);
-    k_inner_final<<<1, 32, 0, s>>>(partial, kBlocks, dV, out);
+    k_inner_final<<<1, 32 * kVals, 0, s>>>(partial, kBlocks, dV, out);
     return cudaGetLastError();
 }
 
