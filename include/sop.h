@@ -202,6 +202,29 @@ int sop_adjoint_gradient(sop_plan plan, const void *phi_dev, int64_t n_steps, do
                          const double *field_samples, int64_t every, double *J, double *grad_field,
                          double *grad_V_dev);
 
+/* Batched propagation (a follow-on of the method: many independent
+ * problems).  A batch groups existing two-dimensional Schroedinger plans of
+ * one dtype and one stream (sides may differ; each plan keeps its lattice,
+ * potential, bound state and tables).  sop_batch_step advances every plan by
+ * n_steps Strang steps of size dt exactly as sop_step would (Eqs. 6-8 with
+ * the split of Eqs. 10a-b), in lockstep: per half step one persistent launch
+ * per pass kind and per pass-axis size, whose tiles are claimed from one
+ * counter across all lattices of that size (the instance is found from the
+ * tile index; sizes without a persistent kernel, e.g. some complex128 sides
+ * with a factor 3, take one-shot passes per lattice).  field_samples[i]
+ * holds plan i's samples as for sop_step
+ * (n_steps x 2, host) or NULL; field_samples itself may be NULL.
+ * Asynchronous on the plans' stream; errors of the persistent kernels are
+ * reported by the next synchronising call on the first plan.  The batch
+ * borrows the plans: destroy the batch before them.  sop_batch_create
+ * returns SOP_EUNSUPPORTED for other plan kinds, SOP_EINVAL for mixed dtypes
+ * or streams or a repeated plan; sop_batch_step SOP_ESTATE when a plan has
+ * no bound state. */
+typedef struct sop_batch_s *sop_batch;
+int sop_batch_create(sop_batch *out, int n_plans, const sop_plan *plans);
+int sop_batch_step(sop_batch batch, int64_t n_steps, double dt, const double *const *field_samples);
+int sop_batch_destroy(sop_batch batch);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *sop_last_error(void);
 

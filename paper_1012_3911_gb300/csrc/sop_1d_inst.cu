@@ -63,9 +63,14 @@ bool pass_geometry(bool f64, int n, int nc, bool contig, int *threads, int *penc
 }
 
 namespace {
+// Pencils per CTA of the persistent pass, 0 where it does not fit on an SM.
+template <typename Real, int N, int NC, bool CONTIG> int async_wp_fit() {
+    using Cfg = AsyncCfg<Real, N, NC, CONTIG>;
+    return Cfg::FITS ? Cfg::WP : 0;
+}
 template <typename Real, int N> int async_wp_of(int nc, bool contig) {
-    if (nc == 1) return contig ? AsyncCfg<Real, N, 1, true>::WP : AsyncCfg<Real, N, 1, false>::WP;
-    return contig ? AsyncCfg<Real, N, 2, true>::WP : AsyncCfg<Real, N, 2, false>::WP;
+    if (nc == 1) return contig ? async_wp_fit<Real, N, 1, true>() : async_wp_fit<Real, N, 1, false>();
+    return contig ? async_wp_fit<Real, N, 2, true>() : async_wp_fit<Real, N, 2, false>();
 }
 }  // namespace
 

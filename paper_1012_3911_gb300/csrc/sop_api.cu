@@ -24,6 +24,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "sop.h"
@@ -482,6 +483,54 @@ void mixing_blocks(const sop_plan p, const double *A, double dt, cd R[2][2][2]) 
     }
 }
 
+// Laser rows of a Schroedinger call: which axes carry a field, where each
+// axis starts in a row of the field tables, the row length.
+struct FieldRows {
+    int active[3] = {0, 0, 0};
+    bool any = false;
+    int64_t offs[3] = {0, 0, 0};
+    int64_t row_len = 0;
+};
+
+// Field vectors of the real-space factors of n steps, f_P = -q tau/(2 hbar)
+// (E_{P-1} + E_P) for P = 0..n (the laser part of exp(-i tau W/(2 hbar)) of
+// both adjacent half steps), uploaded to p->fvec; the rows are built per
+// chunk by build_field_tables.
+int prepare_fields(sop_plan p, int64_t n, double dt, const double *field, FieldRows &fr) {
+    const int nd = p->ndim;
+    auto sample = [&](int64_t s, int a) -> double {
+        return (field && s >= 0 && s < n) ? field[s * nd + a] : 0.0;
+    };
+    if (field)
+        for (int64_t s = 0; s < n; ++s)
+            for (int a = 0; a < nd; ++a)
+                if (field[s * nd + a] != 0.0) fr.active[a] = 1;
+    fr.any = fr.active[0] || fr.active[1] || fr.active[2];
+    if (fr.any) {
+        if (p->fvec_cap < (n + 1) * nd) {
+            cudaStreamSynchronize(p->stream);
+            dfree(p->fvec);
+            p->fvec = nullptr;
+            p->fvec_cap = 0;
+            int rc = dalloc(&p->fvec, (size_t)(n + 1) * nd * sizeof(double), "field vectors");
+            if (rc) return rc;
+            p->fvec_cap = (n + 1) * nd;
+        }
+        std::vector<double> fv((size_t)(n + 1) * nd);
+        const double k = -p->prm.charge * dt / (2.0 * p->prm.hbar);
+        for (int64_t P = 0; P <= n; ++P)
+            for (int a = 0; a < nd; ++a) fv[P * nd + a] = k * (sample(P - 1, a) + sample(P, a));
+        int rc = upload(p, p->fvec, fv.data(), (int64_t)fv.size());
+        if (rc) return rc;
+    }
+    for (int a = 0; a < nd; ++a)
+        if (fr.active[a]) {
+            fr.offs[a] = fr.row_len;
+            fr.row_len += p->dims[a];
+        }
+    return SOP_OK;
+}
+
 int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
     if (!p) return fail(SOP_EINVAL, "sop_step: null plan");
     if (!p->psi) return fail(SOP_ESTATE, "sop_step: no state bound (call sop_bind_state first)");
@@ -542,38 +591,13 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
     }
 
     // ---- Schroedinger -------------------------------------------------------
-    // Field vectors of the real-space factors: f_P = -q tau/(2 hbar) (E_{P-1} + E_P),
-    // the laser part of exp(-i tau W/(2 hbar)) of both adjacent half steps.
-    int active[3] = {0, 0, 0};
-    if (field)
-        for (int64_t s = 0; s < n; ++s)
-            for (int a = 0; a < nd; ++a)
-                if (field[s * nd + a] != 0.0) active[a] = 1;
-    const bool any_field = active[0] || active[1] || active[2];
-    if (any_field) {
-        if (p->fvec_cap < (n + 1) * nd) {
-            cudaStreamSynchronize(p->stream);
-            dfree(p->fvec);
-            p->fvec = nullptr;
-            p->fvec_cap = 0;
-            rc = dalloc(&p->fvec, (size_t)(n + 1) * nd * sizeof(double), "field vectors");
-            if (rc) return rc;
-            p->fvec_cap = (n + 1) * nd;
-        }
-        std::vector<double> fv((size_t)(n + 1) * nd);
-        const double k = -p->prm.charge * dt / (2.0 * hbar);
-        for (int64_t P = 0; P <= n; ++P)
-            for (int a = 0; a < nd; ++a) fv[P * nd + a] = k * (sample(P - 1, a) + sample(P, a));
-        rc = upload(p, p->fvec, fv.data(), (int64_t)fv.size());
-        if (rc) return rc;
-    }
-    int64_t offs[3] = {0, 0, 0};
-    int64_t row_len = 0;
-    for (int a = 0; a < nd; ++a)
-        if (active[a]) {
-            offs[a] = row_len;
-            row_len += p->dims[a];
-        }
+    FieldRows fr;
+    rc = prepare_fields(p, n, dt, field, fr);
+    if (rc) return rc;
+    const int *active = fr.active;
+    const bool any_field = fr.any;
+    const int64_t *offs = fr.offs;
+    const int64_t row_len = fr.row_len;
 
     for (int64_t P0 = 0; P0 <= n; P0 += kFieldChunk) {
         const int64_t P1 = std::min<int64_t>(n + 1, P0 + kFieldChunk);
@@ -946,6 +970,269 @@ int sop_profile_read(sop_plan p, double *ms, int64_t *launches, int max_classes)
 }
 
 int64_t sop_launch_counter(sop_plan p) { return p ? p->launches : 0; }
+
+// ---------------------------------------------------------------------------
+// Batched propagation: independent 2D Schroedinger lattices of uneven sizes
+// advanced in lockstep, one multi-instance launch per pass kind and per
+// pass-axis size (lattices sharing that size share the launch's tiles).
+// ---------------------------------------------------------------------------
+
+}  // extern "C"
+
+struct sop_batch_s {
+    std::vector<sop_plan> plans;
+    cudaStream_t stream = nullptr;
+    bool f64 = false;
+    unsigned long long *tile_ctr = nullptr;
+    unsigned long long tile_base = 0;
+    InstDesc *desc = nullptr;
+    size_t desc_cap = 0;   // descriptors
+};
+
+namespace {
+
+int batch_free(sop_batch b) {
+    if (!b) return SOP_OK;
+    cudaStreamSynchronize(b->stream);
+    dfree(b->tile_ctr);
+    dfree(b->desc);
+    delete b;
+    return SOP_OK;
+}
+
+// One multi-instance pass over the lattices of a group.
+int batch_launch(sop_batch b, PassArgs &a, bool contig, const char *what) {
+    sop_plan p0 = b->plans[0];
+    a.errflag = p0->errflag;
+    a.tile_ctr = b->tile_ctr;
+    a.tile_base[0] = a.tile_base[1] = b->tile_base;
+    a.n_comp_total = 1;
+    TensorMapBytes tm;
+    std::memset(&tm, 0, sizeof(tm));
+    int64_t adv = 0;
+    cudaError_t e;
+    if (b->f64)
+        e = contig ? launch_async_f64_contig(a, 1, tm, b->stream, &adv) : launch_async_f64_strided(a, 1, tm, b->stream, &adv);
+    else
+        e = contig ? launch_async_f32_contig(a, 1, tm, b->stream, &adv) : launch_async_f32_strided(a, 1, tm, b->stream, &adv);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    b->tile_base += (unsigned long long)adv;
+    p0->launches += 1;
+    return SOP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sop_batch_create(sop_batch *out, int n_plans, const sop_plan *plans) {
+    if (!out) return fail(SOP_EINVAL, "sop_batch_create: out is NULL");
+    *out = nullptr;
+    if (n_plans < 1 || !plans) return fail(SOP_EINVAL, "sop_batch_create: no plans");
+    for (int i = 0; i < n_plans; ++i) {
+        const sop_plan p = plans[i];
+        if (!p) return fail(SOP_EINVAL, "sop_batch_create: null plan");
+        if (p->comps != 1 || p->ndim != 2)
+            return fail(SOP_EUNSUPPORTED, "sop_batch_create: two-dimensional Schroedinger plans only");
+        if (p->f64 != plans[0]->f64 || p->stream != plans[0]->stream)
+            return fail(SOP_EINVAL, "sop_batch_create: plans differ in dtype or stream");
+
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == p) return fail(SOP_EINVAL, "sop_batch_create: a plan appears twice");
+    }
+    sop_batch b = new sop_batch_s();
+    b->plans.assign(plans, plans + n_plans);
+    b->stream = plans[0]->stream;
+    b->f64 = plans[0]->f64;
+    int rc = dalloc(&b->tile_ctr, 2 * sizeof(unsigned long long), "batch tile counters");
+    if (!rc) {
+        cudaError_t e = cudaMemsetAsync(b->tile_ctr, 0, 2 * sizeof(unsigned long long), b->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync(batch tile counters)");
+    }
+    if (rc) {
+        batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return SOP_OK;
+}
+
+int sop_batch_destroy(sop_batch b) { return batch_free(b); }
+
+int sop_batch_step(sop_batch b, int64_t n, double dt, const double *const *fields) {
+    if (!b) return fail(SOP_EINVAL, "sop_batch_step: null batch");
+    if (n < 0) return fail(SOP_EINVAL, "sop_batch_step: n_steps < 0");
+    if (!is_finite(dt)) return fail(SOP_EINVAL, "sop_batch_step: dt is not finite");
+    if (n == 0) return SOP_OK;
+    const int np = (int)b->plans.size();
+    std::vector<FieldRows> fr((size_t)np);
+    for (int i = 0; i < np; ++i) {
+        sop_plan p = b->plans[i];
+        if (!p->psi) return fail(SOP_ESTATE, "sop_batch_step: a plan has no state bound");
+        const double *f = fields ? fields[i] : nullptr;
+        if (f)
+            for (int64_t k = 0; k < n * 2; ++k)
+                if (!is_finite(f[k])) return fail(SOP_EINVAL, "sop_batch_step: field sample is not finite");
+        int rc = ensure_tables(p, dt);
+        if (rc) return rc;
+        rc = prepare_fields(p, n, dt, f, fr[(size_t)i]);
+        if (rc) return rc;
+    }
+    // groups by pass-axis size: the x passes by n_x, the y passes by n_y
+    struct Group {
+        int axis;
+        bool multi = false;   // one multi-instance launch (else one-shot passes per lattice)
+        std::vector<int> members;
+        int64_t first = 0, tiles = 0;
+    };
+    std::map<int64_t, Group> gx, gy;
+    for (int i = 0; i < np; ++i) {
+        gx[b->plans[i]->dims[0]].members.push_back(i);
+        gy[b->plans[i]->dims[1]].members.push_back(i);
+    }
+    for (auto &kv : gx) kv.second.axis = 0;
+    for (auto &kv : gy) kv.second.axis = 1;
+    std::vector<InstDesc> hd;
+    for (auto *gm : {&gx, &gy})
+        for (auto &kv : *gm) {
+            Group &g = kv.second;
+            g.first = (int64_t)hd.size();
+            const int axis = g.axis;
+            const int wp = async_pencils_per_cta(b->f64, (int)kv.first, 1, axis == 0);
+            g.multi = wp > 0 && b->plans[g.members[0]]->async_passes;
+            if (!g.multi) continue;
+            int64_t tiles = 0;
+            for (int i : g.members) {
+                sop_plan p = b->plans[i];
+                InstDesc d;
+                std::memset(&d, 0, sizeof(d));
+                d.psi = p->psi;
+                d.vhalf = p->v_set ? p->vhalf : nullptr;
+                d.vfull = p->v_set ? p->vfull : nullptr;
+                const FieldRows &f = fr[(size_t)i];
+                d.ftab = f.any ? p->ftab : nullptr;
+                d.frow_len = f.row_len;
+                for (int a = 0; a < 3; ++a) {
+                    d.foff[a] = (a < 2 && f.active[a]) ? f.offs[a] : -1;
+                    d.ttab[a] = a < 2 ? p->kin[a] : nullptr;
+                    d.dims[a] = p->dims[a];
+                }
+                d.n_pencils = p->npts / p->dims[axis];
+                if (axis == 0) {
+                    d.n_xgroups = 0;
+                    d.tile_begin = tiles;
+                    tiles += (d.n_pencils + wp - 1) / wp;
+                } else {
+                    d.n_xgroups = (p->dims[0] + wp - 1) / wp;
+                    d.o_stride = 0;
+                    d.tiles_per_batch = d.n_xgroups * (d.n_pencils / p->dims[0]);
+                    d.tile_begin = tiles;
+                    tiles += d.n_xgroups;
+                    TensorMapBytes tm;
+                    int rc = tensor_map(p, p->psi, 1, 1, &tm);
+                    if (rc) return rc;
+                    std::memcpy(d.tmap, tm.b, sizeof(d.tmap));
+                }
+                d.scale_hi = p->scale_hi;
+                d.scale_lo = p->scale_lo;
+                hd.push_back(d);
+            }
+            g.tiles = tiles;
+        }
+    if (!hd.empty() && b->desc_cap < hd.size()) {
+        cudaStreamSynchronize(b->stream);
+        dfree(b->desc);
+        b->desc = nullptr;
+        b->desc_cap = 0;
+        int rc = dalloc(&b->desc, hd.size() * sizeof(InstDesc), "batch descriptors");
+        if (rc) return rc;
+        b->desc_cap = hd.size();
+    }
+    static_assert(sizeof(InstDesc) % sizeof(double) == 0, "descriptor size");
+    int rc = SOP_OK;
+    if (!hd.empty()) {
+        rc = upload(b->plans[0], reinterpret_cast<double *>(b->desc), reinterpret_cast<const double *>(hd.data()),
+                    (int64_t)(hd.size() * sizeof(InstDesc) / sizeof(double)));
+        if (rc) return rc;
+    }
+    // one-shot pass of one lattice (groups without a persistent kernel)
+    auto single = [&](int i, int axis, int pre, int post, int op, int64_t P, int64_t P0, const char *what) -> int {
+        sop_plan p = b->plans[i];
+        const FieldRows &f = fr[(size_t)i];
+        PassArgs a;
+        base_args(p, a, p->psi, axis);
+        a.pre = pre;
+        a.post = post;
+        a.op = op;
+        if (op == OP_V) {
+            a.vtab = p->v_set ? ((P == 0 || P == n) ? p->vhalf : p->vfull) : nullptr;
+            for (int ax = 0; ax < 2; ++ax)
+                a.ftab[ax] = f.active[ax] ? static_cast<const char *>(p->ftab) + ((P - P0) * f.row_len + f.offs[ax]) * p->csz
+                                          : nullptr;
+        } else {
+            for (int ax = 0; ax < 2; ++ax) a.ttab[ax] = p->kin[ax];
+        }
+        return launch_pass(p, a, 1, what);
+    };
+    for (int64_t P0 = 0; P0 <= n; P0 += kFieldChunk) {
+        const int64_t P1 = std::min<int64_t>(n + 1, P0 + kFieldChunk);
+        for (int i = 0; i < np; ++i) {
+            sop_plan p = b->plans[i];
+            const FieldRows &f = fr[(size_t)i];
+            if (!f.any) continue;
+            cudaError_t e = build_field_tables(p->ftab, p->fvec + P0 * 2, P1 - P0, 2, p->dims, p->h, f.active,
+                                               f.offs, f.row_len, p->f64, p->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "build_field_tables");
+            p->launches += 1;
+        }
+        for (int64_t P = P0; P < P1; ++P) {
+            for (auto &kv : gx) {
+                Group &g = kv.second;
+                if (!g.multi) {
+                    for (int i : g.members)
+                        if ((rc = single(i, 0, P > 0 ? +1 : 0, P < n ? -1 : 0, OP_V, P, P0, "real-space pass"))) return rc;
+                    continue;
+                }
+                sop_plan p0 = b->plans[g.members[0]];
+                PassArgs a;
+                base_args(p0, a, p0->psi, 0);
+                a.pre = P > 0 ? +1 : 0;
+                a.post = P < n ? -1 : 0;
+                a.op = OP_V;
+                a.inst = b->desc + g.first;
+                a.n_inst = (int)g.members.size();
+                a.P = P;
+                a.p_table0 = P0;
+                a.n_total = n;
+                a.n_tiles = g.tiles;
+                if ((rc = batch_launch(b, a, true, "batched real-space pass"))) return rc;
+            }
+            if (P == n) break;
+            for (auto &kv : gy) {
+                Group &g = kv.second;
+                if (!g.multi) {
+                    for (int i : g.members)
+                        if ((rc = single(i, 1, -1, +1, OP_T, P, P0, "momentum-space pass"))) return rc;
+                    continue;
+                }
+                sop_plan p0 = b->plans[g.members[0]];
+                PassArgs a;
+                base_args(p0, a, p0->psi, 1);
+                a.pre = -1;
+                a.post = +1;
+                a.op = OP_T;
+                a.inst = b->desc + g.first;
+                a.n_inst = (int)g.members.size();
+                a.P = P;
+                a.p_table0 = P0;
+                a.n_total = n;
+                a.n_tiles = g.tiles;
+                if ((rc = batch_launch(b, a, false, "batched momentum-space pass"))) return rc;
+            }
+        }
+    }
+    return SOP_OK;
+}
 
 int sop_adjoint_gradient(sop_plan p, const void *phi_dev, int64_t n_steps, double dt, const double *field,
                          int64_t every, double *J, double *grad_field, double *grad_V_dev) {

@@ -230,9 +230,13 @@ template <typename Real, int N, int NC, bool CONTIG> struct AsyncCfg {
 // The kernel
 // ---------------------------------------------------------------------------
 
-template <typename Real, int N, int NC, bool CONTIG>
+// MULTI: the tiles belong to several lattices (a.inst, one component each)
+// that share the pass-axis size N; each tile takes its lattice's state,
+// tables, geometry and tensor map from the instance descriptor.
+template <typename Real, int N, int NC, bool CONTIG, bool MULTI>
 __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncCfg<Real, N, NC, CONTIG>::MINB)
     pass_kernel_async(const __grid_constant__ PassArgs a, const __grid_constant__ CUtensorMap tmap) {
+    static_assert(!MULTI || NC == 1, "multi-instance passes have one component");
     using Cfg = AsyncCfg<Real, N, NC, CONTIG>;
     using C = cplx_t<Real>;
     using Ph = Phase<Real>;
@@ -250,7 +254,6 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
     const int pz = NC == 2 ? (int)blockIdx.z : 0;
     const int64_t stride = CONTIG ? 1 : a.stride;
     const bool op_v = a.op == OP_V, op_t = a.op == OP_T;
-    const bool want_v = CONTIG && a.vtab != nullptr && (op_v || a.op == OP_DV);
     // the factor table of this pass's axis (field row for OP_V, kinetic row for OP_T)
     const C *axsrc = nullptr;
     if (NC == 1 && (op_v || op_t)) {
@@ -258,7 +261,6 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
                              : (a.axis == 0 ? a.ttab[0] : (a.axis == 1 ? a.ttab[1] : a.ttab[2]));
         axsrc = reinterpret_cast<const C *>(p);
     }
-    C *psi = reinterpret_cast<C *>(a.psi);
     const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]), barx = smem_addr(&bars[2]);
 
     const int64_t ntiles = a.n_tiles;
@@ -280,19 +282,90 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
     if constexpr (!Cfg::LEAN) StageTable<C, N, E>::fill(twz, reinterpret_cast<const C *>(a.tw), tid, Cfg::THREADS);
     __syncthreads();
 
-    const int64_t per_batch = a.n_pencils;
-    const int64_t total = (NC == 1) ? per_batch * a.n_batch : per_batch;
-    const int64_t n0 = a.dims[0];
-    const int64_t tiles_per_batch = CONTIG ? 0 : a.n_xgroups * (per_batch / n0);
+    // Multi-instance: the lattice of global tile g (the last instance whose
+    // first tile is <= g).
+    auto find_inst = [&](int64_t g) -> const InstDesc * {
+        int lo = 0, hi = a.n_inst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.inst[mid].tile_begin <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        return a.inst + lo;
+    };
+    // Per-tile values, read where they are used (launch arguments of a
+    // single lattice, or the instance descriptor through L1), so that they
+    // hold no registers across the tile.
+    auto pv_psi = [&](const InstDesc *d) -> C * {
+        if constexpr (MULTI) return reinterpret_cast<C *>(d->psi);
+        else return reinterpret_cast<C *>(a.psi);
+    };
+    auto pv_vtab = [&](const InstDesc *d) -> const C * {
+        if constexpr (MULTI) return reinterpret_cast<const C *>((a.P == 0 || a.P == a.n_total) ? d->vhalf : d->vfull);
+        else return reinterpret_cast<const C *>(a.vtab);
+    };
+    auto pv_row = [&](const InstDesc *d, int ax) -> const C * {   // factor row of axis ax (field or kinetic)
+        if constexpr (MULTI) {
+            if (!op_v) return reinterpret_cast<const C *>(d->ttab[ax]);
+            if (!d->ftab || d->foff[ax] < 0) return nullptr;
+            return reinterpret_cast<const C *>(d->ftab) + (a.P - a.p_table0) * d->frow_len + d->foff[ax];
+        } else {
+            return reinterpret_cast<const C *>(op_v ? a.ftab[ax] : a.ttab[ax]);
+        }
+    };
+    const int64_t tpb_single = CONTIG ? 0 : a.n_xgroups * (a.n_pencils / a.dims[0]);
+    auto pv_i64 = [&](const InstDesc *d, int which) -> int64_t {
+        // 0 pencils per batch, 1 pencils, 2 n0, 3 n1, 4 x groups, 5 o stride,
+        // 6 component stride, 7 strided tiles per batch entry
+        if constexpr (MULTI) {
+            switch (which) {
+                case 0: case 1: return d->n_pencils;
+                case 2: return d->dims[0];
+                case 3: return d->dims[1];
+                case 4: return d->n_xgroups;
+                case 5: return d->o_stride;
+                case 7: return d->tiles_per_batch;
+                default: return 0;
+            }
+        } else {
+            switch (which) {
+                case 0: return a.n_pencils;
+                case 1: return (NC == 1) ? a.n_pencils * a.n_batch : a.n_pencils;
+                case 2: return a.dims[0];
+                case 3: return a.dims[1];
+                case 4: return a.n_xgroups;
+                case 5: return a.o_stride;
+                case 7: return tpb_single;
+                default: return a.comp_stride;
+            }
+        }
+    };
+    auto pv_map = [&](const InstDesc *d) -> const CUtensorMap * {
+        if constexpr (MULTI) return reinterpret_cast<const CUtensorMap *>(d->tmap);
+        else return &tmap;
+    };
+    // Global tile g -> its lattice (null for a single lattice) and local index.
+    auto locate = [&](int64_t g, int64_t &local) -> const InstDesc * {
+        if constexpr (MULTI) {
+            const InstDesc *d = find_inst(g);
+            local = g - d->tile_begin;
+            return d;
+        } else {
+            local = g;
+            return nullptr;
+        }
+    };
 
     auto comp_index = [&](int c, int64_t b) -> int64_t {
         return NC == 1 ? b : (int64_t)a.pair_comp[pz][c];
     };
 
-    // Strided axes: the TMA boxes of tile tl, f(component slot, box, coords...)
-    // with coordinates (x [in 8-byte units], axis 1, axis 2, component).
-    auto tile_boxes = [&](int64_t tl, auto &&f) {
-        const uint32_t ut = (uint32_t)tl, ng = (uint32_t)a.n_xgroups;
+    // Strided axes: the TMA boxes of tile tl of lattice q, f(component slot,
+    // box, coords...) with coordinates (x [in 8-byte units], axis 1, axis 2,
+    // component).
+    auto tile_boxes = [&](const InstDesc *d, int64_t tl, auto &&f) {
+        const int64_t tiles_per_batch = pv_i64(d, 7);
+        const uint32_t ut = (uint32_t)tl, ng = (uint32_t)pv_i64(d, 4);
         const uint32_t bidx = NC == 1 ? ut / (uint32_t)tiles_per_batch : 0u;
         const uint32_t rem = NC == 1 ? ut - bidx * (uint32_t)tiles_per_batch : ut;
         const uint32_t o = rem / ng;
@@ -308,8 +381,11 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         }
     };
 
-    // Thread 0: start the copies of tile tl into buffer slot b.
-    auto issue = [&](int64_t tl, int b) {
+    // Thread 0: start the copies of (global) tile g into buffer slot b.
+    auto issue = [&](int64_t g, int b) {
+        int64_t tl;
+        const InstDesc *d = locate(g, tl);
+        const int64_t per_batch = pv_i64(d, 0), total = pv_i64(d, 1);
         const uint32_t bar = b ? bar1 : bar0;
         const uint32_t dst0 = smem_addr(buf0 + b * Cfg::BUF);
         if constexpr (CONTIG) {
@@ -324,26 +400,31 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
                     pp = p - bidx * per_batch;
                 }
                 for (int c = 0; c < NC; ++c) {
-                    const int64_t off = comp_index(c, bidx) * a.comp_stride + pp * N;
-                    bulk_g2s(dst0 + (uint32_t)((r * NC + c) * Cfg::PITCH * CSZ), psi + off, (uint32_t)(N * CSZ), bar);
+                    const int64_t off = comp_index(c, bidx) * pv_i64(d, 6) + pp * N;
+                    bulk_g2s(dst0 + (uint32_t)((r * NC + c) * Cfg::PITCH * CSZ), pv_psi(d) + off, (uint32_t)(N * CSZ),
+                             bar);
                 }
             }
         } else {
             mbar_expect_tx(bar, (uint32_t)(NC * N * WP * CSZ));
-            tile_boxes(tl, [&](int c, int r, int c0, int c1, int c2, int c3) {
+            const CUtensorMap *map = pv_map(d);
+            tile_boxes(d, tl, [&](int c, int r, int c0, int c1, int c2, int c3) {
                 const uint32_t dst = dst0 + (uint32_t)((c * N + r * Cfg::BR) * WP * CSZ);
-                if (a.ndim == 2) tma_load_3d(dst, &tmap, c0, c1, c3, bar);
-                else tma_load_4d(dst, &tmap, c0, c1, c2, c3, bar);
+                if (a.ndim == 2) tma_load_3d(dst, map, c0, c1, c3, bar);
+                else tma_load_4d(dst, map, c0, c1, c2, c3, bar);
             });
         }
     };
-    // Thread 0: write tile tl back from buffer slot b (strided axes).
-    auto store_tile = [&](int64_t tl, int b) {
+    // Thread 0: write (global) tile g back from buffer slot b (strided axes).
+    auto store_tile = [&](int64_t g, int b) {
+        int64_t tl;
+        const InstDesc *d = locate(g, tl);
+        const CUtensorMap *map = pv_map(d);
         const uint32_t src0 = smem_addr(buf0 + b * Cfg::BUF);
-        tile_boxes(tl, [&](int c, int r, int c0, int c1, int c2, int c3) {
+        tile_boxes(d, tl, [&](int c, int r, int c0, int c1, int c2, int c3) {
             const uint32_t src = src0 + (uint32_t)((c * N + r * Cfg::BR) * WP * CSZ);
-            if (a.ndim == 2) tma_store_3d(&tmap, c0, c1, c3, src);
-            else tma_store_4d(&tmap, c0, c1, c2, c3, src);
+            if (a.ndim == 2) tma_store_3d(map, c0, c1, c3, src);
+            else tma_store_4d(map, c0, c1, c2, c3, src);
         });
         bulk_commit();
     };
@@ -359,8 +440,9 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         }
     };
 
-    const bool has_axt = axsrc != nullptr;
-    const bool axt_smem = !Cfg::LEAN && has_axt;   // axis table copied into shared memory
+    // axis table copied into shared memory (single lattice; multi-instance
+    // passes read each lattice's row through L1)
+    const bool axt_smem = !Cfg::LEAN && !MULTI && axsrc != nullptr;
     // Before this point only the stage twiddles (written when the plan was
     // made) are read.  psi and the phase tables may come from the kernel
     // just before this one in the stream.
@@ -421,6 +503,15 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         };
         if (CONTIG && tid == 0) claim_next();
 
+        int64_t ltile = tile;
+        const InstDesc *dp = nullptr;
+        if constexpr (MULTI) {
+            dp = find_inst(tile);
+            ltile = tile - dp->tile_begin;
+        }
+        const int64_t per_batch = pv_i64(dp, 0), total = pv_i64(dp, 1), n0 = pv_i64(dp, 2);
+        const int64_t tiles_per_batch = pv_i64(dp, 7);
+        const bool want_v = CONTIG && pv_vtab(dp) != nullptr && (op_v || a.op == OP_DV);
         // Pencil of this thread: first point (linear index base) and lattice
         // coordinates co (0 along the pass axis).  Pencil and tile counts are
         // below 2^31, so the index arithmetic runs in 32 bits.
@@ -428,7 +519,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         int co[3] = {0, 0, 0};
         bool active;
         if constexpr (CONTIG) {
-            const uint32_t p = (uint32_t)tile * WP + w;
+            const uint32_t p = (uint32_t)ltile * WP + w;
             active = p < (uint32_t)total;
             const uint32_t pc = active ? p : 0u;
             uint32_t bidx = 0, pp = pc;
@@ -437,31 +528,31 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
                 pp = pc - bidx * (uint32_t)per_batch;
             }
             base = (int64_t)pp * N;
-            const uint32_t n1 = (uint32_t)a.dims[1];
+            const uint32_t n1 = (uint32_t)pv_i64(dp, 3);
             if (a.ndim >= 2) co[1] = (int)(pp % n1);
             if (a.ndim == 3) co[2] = (int)(pp / n1);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) coff[c] = comp_index(c, bidx) * a.comp_stride;
+            for (int c = 0; c < NC; ++c) coff[c] = comp_index(c, bidx) * pv_i64(dp, 6);
         } else {
-            const uint32_t ut = (uint32_t)tile, ng = (uint32_t)a.n_xgroups;
+            const uint32_t ut = (uint32_t)ltile, ng = (uint32_t)pv_i64(dp, 4);
             const uint32_t bidx = NC == 1 ? ut / (uint32_t)tiles_per_batch : 0u;
             const uint32_t rem = NC == 1 ? ut - bidx * (uint32_t)tiles_per_batch : ut;
             const uint32_t o = rem / ng;   // the remaining coordinate (z for axis 1, y for axis 2)
             const uint32_t x = (rem - o * ng) * WP + w;
             active = x < (uint32_t)n0;
             const uint32_t xc = active ? x : 0u;
-            base = (int64_t)xc + (int64_t)o * a.o_stride;
+            base = (int64_t)xc + (int64_t)o * pv_i64(dp, 5);
             co[0] = (int)xc;
             if (a.ndim == 3) co[a.axis == 1 ? 2 : 1] = (int)o;
 #pragma unroll
-            for (int c = 0; c < NC; ++c) coff[c] = comp_index(c, bidx) * a.comp_stride;
+            for (int c = 0; c < NC; ++c) coff[c] = comp_index(c, bidx) * pv_i64(dp, 6);
         }
 
         // Per-point phase values of this pencil, fetched now and used after
         // the first transform (bypassing L1).
         C vpre[E];
         if (want_v) {
-            const C *vt = reinterpret_cast<const C *>(a.vtab) + base;
+            const C *vt = pv_vtab(dp) + base;
 #pragma unroll
             for (int m = 0; m < E; ++m) vpre[m] = ld_stream(vt + (t + T * m));
         } else {
@@ -513,8 +604,9 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
                 // the loop is specialised on them rather than branching per point.
                 const C *tab[3];
 #pragma unroll
-                for (int ax = 0; ax < 3; ++ax)
-                    tab[ax] = reinterpret_cast<const C *>(op_v ? a.ftab[ax] : a.ttab[ax]);
+                for (int ax = 0; ax < 3; ++ax) tab[ax] = pv_row(dp, ax);
+                const C *const axsrc_t = (MULTI || Cfg::LEAN) ? pv_row(dp, a.axis) : axsrc;
+                const bool has_axt = axsrc_t != nullptr;
                 C g = Ph::one();
                 bool g_set = false;
 #pragma unroll
@@ -524,8 +616,15 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
                         g = g_set ? Ph::combine(g, x) : x;
                         g_set = true;
                     }
-                const Real shi = Real(a.scale_hi), slo = Real(a.scale_lo);
-                auto axis_at = [&](int i) -> C { return Cfg::LEAN ? ldg_c(axsrc + i) : axt[i]; };
+                Real shi, slo;
+                if constexpr (MULTI) {
+                    shi = Real(dp->scale_hi);
+                    slo = Real(dp->scale_lo);
+                } else {
+                    shi = Real(a.scale_hi);
+                    slo = Real(a.scale_lo);
+                }
+                auto axis_at = [&](int i) -> C { return (Cfg::LEAN || MULTI) ? ldg_c(axsrc_t + i) : axt[i]; };
                 // f = [V phase] [axis factor] [g], then psi <- psi (1 + f) [* 1/N].
                 auto loop = [&](auto hv_c, auto axt_c, auto g_c, auto scale_c) {
                     constexpr bool HV = decltype(hv_c)::value, AX = decltype(axt_c)::value;
@@ -601,9 +700,9 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
             if (active) {
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    C *q = psi + coff[c] + base + t;
+                    C *dst = pv_psi(dp) + coff[c] + base + t;
 #pragma unroll
-                    for (int m = 0; m < E; ++m) st_stream(q + T * m, v[c][m]);
+                    for (int m = 0; m < E; ++m) st_stream(dst + T * m, v[c][m]);
                 }
             }
             __syncthreads();   // the tile buffer is free again; s_tile of the next iteration is set
@@ -664,19 +763,25 @@ cudaError_t launch_async_t(const PassArgs &a0, const TensorMapBytes &tm, cudaStr
         return cudaErrorInvalidValue;
     } else {
         PassArgs a = a0;
-        const int64_t total = (NC == 1) ? a.n_pencils * a.n_batch : a.n_pencils;
-        if (CONTIG) {
-            a.n_xgroups = 0;
-            a.n_tiles = (total + Cfg::WP - 1) / Cfg::WP;
-        } else {
-            const int64_t n0 = a.dims[0];
-            a.n_xgroups = (n0 + Cfg::WP - 1) / Cfg::WP;
-            const int64_t others = a.n_pencils / n0;
-            a.n_tiles = a.n_xgroups * others * (NC == 1 ? a.n_batch : 1);
+        // multi-instance launches: the host set n_tiles and the instance descriptors
+        const bool multi = NC == 1 && a.inst != nullptr;
+        if (!multi) {
+            const int64_t total = (NC == 1) ? a.n_pencils * a.n_batch : a.n_pencils;
+            if (CONTIG) {
+                a.n_xgroups = 0;
+                a.n_tiles = (total + Cfg::WP - 1) / Cfg::WP;
+            } else {
+                const int64_t n0 = a.dims[0];
+                a.n_xgroups = (n0 + Cfg::WP - 1) / Cfg::WP;
+                const int64_t others = a.n_pencils / n0;
+                a.n_tiles = a.n_xgroups * others * (NC == 1 ? a.n_batch : 1);
+            }
         }
         *ctr_advance = 0;
         if (a.n_tiles <= 0) return cudaSuccess;
-        auto kern = pass_kernel_async<Real, N, NC, CONTIG>;
+        auto kern = pass_kernel_async<Real, N, NC, CONTIG, false>;
+        if constexpr (NC == 1)
+            if (multi) kern = pass_kernel_async<Real, N, NC, CONTIG, true>;
         cudaError_t e = ensure_smem_attr(reinterpret_cast<const void *>(kern), (int)Cfg::SMEM);
         if (e != cudaSuccess) return e;
         int per_sm = 0, sms = 0;

@@ -18,6 +18,8 @@ enum PassOp : int {
 
 // Arguments of one pencil pass along one axis.  A "pencil" is the set of
 // n = dims[axis] points that differ only in the axis index.
+struct InstDesc;
+
 struct PassArgs {
     void *psi;               // complex array of the plan's dtype
     int64_t comp_stride;     // points per component (prod dims)
@@ -52,10 +54,35 @@ struct PassArgs {
     // (every CTA ends with one claim past the last tile).
     unsigned long long *tile_ctr;
     unsigned long long tile_base[2];
+    // Multi-instance passes (inst != null): tiles of n_inst lattices that
+    // share the pass-axis size; P is the real-space index of the launch
+    // (its row in each instance's field table is P - p_table0) and n_total
+    // the step count of the call (P = 0 and P = n_total take the half factor).
+    const InstDesc *inst;
+    int n_inst;
+    int64_t P, p_table0, n_total;
     int64_t n_tiles;         // tiles of the pass (per component pair for nc == 2)
     int64_t n_xgroups;       // strided: tiles along x
     int64_t o_stride;        // strided: element stride of the remaining coordinate
     int n_comp_total;        // components in the array (tensor-map outer extent)
+};
+
+// One lattice of a multi-instance pass (device memory; a batch of
+// independent Schroedinger problems advanced in lockstep).  The tensor map
+// comes first so that it is 64-byte aligned.
+struct alignas(64) InstDesc {
+    unsigned char tmap[128];   // CUtensorMap of psi for the strided axis of the pass
+    void *psi;
+    const void *vhalf, *vfull; // per-point phase tables (half and merged real-space factor), may be null
+    const void *ftab;          // field tables of the launch's chunk: rows of frow_len, or null
+    const void *ttab[3];       // kinetic rows per axis
+    int64_t foff[3];           // offset of axis a in a field row; -1: no field along a
+    int64_t frow_len;
+    int64_t dims[3];
+    int64_t n_pencils, n_xgroups, o_stride;
+    int64_t tiles_per_batch;   // strided axes: n_xgroups x (pencils / n_x)
+    int64_t tile_begin;        // first global tile of this instance
+    double scale_hi, scale_lo; // 1/N of this lattice
 };
 
 // Arguments of the one-dimensional whole-step kernel.
@@ -111,7 +138,8 @@ cudaError_t launch_grad_v(const double *acc, int64_t npts, double zr, double zi,
 // -1 for a size without persistent passes.
 int stage_table_f32(int n, int nc, void *out, const void *tw, cudaStream_t s);
 int stage_table_f64(int n, int nc, void *out, const void *tw, cudaStream_t s);
-// Pencils per CTA of the asynchronous pass (the tensor-map box width for strided axes).
+// Pencils per CTA of the asynchronous pass (the tensor-map box width for
+// strided axes); 0 when that pass does not fit on an SM (one-shot passes).
 int async_pencils_per_cta(bool f64, int n, int nc, bool contig);
 cudaError_t launch_1d_f32(const Args1D &a, int n, cudaStream_t s);
 cudaError_t launch_1d_f64(const Args1D &a, int n, cudaStream_t s);

@@ -241,6 +241,69 @@ def sop_adjoint_gradient(plan: int, phi, n_steps: int, dt: float, field, every: 
     return J.value, g
 
 
+def sop_batch_create(plans) -> int:
+    """A batch over plan handles (two-dimensional Schroedinger, one dtype and stream)."""
+    lib = load()
+    fn = lib.sop_batch_create
+    fn.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+    fn.restype = ctypes.c_int
+    arr = (ctypes.c_void_p * len(plans))(*plans)
+    out = ctypes.c_void_p()
+    _check(fn(ctypes.byref(out), len(plans), arr))
+    return out.value
+
+
+def sop_batch_step(batch: int, n_steps: int, dt: float, fields=None, ndim: int = 2) -> None:
+    """Asynchronous lockstep steps of every plan; fields: None or a list with
+    one entry (n_steps x ndim samples or None) per plan."""
+    lib = load()
+    fn = lib.sop_batch_step
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    keep, arr = [], None
+    if fields is not None:
+        ptrs = []
+        for f in fields:
+            if f is None:
+                ptrs.append(None)
+            else:
+                k, ptr = _field_ptr(f, n_steps, ndim)
+                keep.append(k)
+                ptrs.append(ptr)
+        arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+    _check(fn(batch, int(n_steps), float(dt), arr))
+    del keep
+
+
+def sop_batch_destroy(batch: int) -> None:
+    lib = load()
+    lib.sop_batch_destroy.argtypes = [ctypes.c_void_p]
+    lib.sop_batch_destroy.restype = ctypes.c_int
+    _check(lib.sop_batch_destroy(batch))
+
+
+class Batch:
+    """Several Propagators advanced together by sop_batch_step."""
+
+    def __init__(self, props):
+        self.props = list(props)
+        self.handle = sop_batch_create([p.plan for p in self.props])
+
+    def step(self, n_steps: int, dt: float, fields=None) -> None:
+        sop_batch_step(self.handle, n_steps, dt, fields, 2)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            sop_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Propagator:
     """A plan plus its bound torch state.
 
