@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--ref-split-steps", type=int, default=2, help="oracle split steps per reference step")
     ap.add_argument("--profile-every", type=int, default=64,
                     help="time the passes of one split step in this many (per-class roofline)")
+    ap.add_argument("--batched", type=int, default=1, help="also time the batched and adjoint forms (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=400, help="split steps of the batched / adjoint sample")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
@@ -271,6 +273,64 @@ def main():
     est = {names[c]: cls_ms[c] / cls_n[c] * k for c, k in per_step.items() if cls_n[c]}
     roofline["pass_ms_share"] = {k: v / sum(est.values()) for k, v in est.items()}
 
+    # ---- batched and adjoint forms (the config-5 workload), complex64 -------
+    batched = None
+    adjoint = None
+    if args.batched and rank == 0:
+        ws = wl.config5(64, n_steps=args.batch_steps)
+        npts5 = sum(x.npoints for x in ws)
+        props = []
+        for x in ws:
+            q = sop.Propagator(x.dims, x.spacing, 1, "c64")
+            q.set_state(torch.from_numpy(x.psi0))
+            q.set_potential(x.V)
+            props.append(q)
+        bat = sop.Batch(props)
+        fields = [x.field for x in ws]
+        bat.step(2, ws[0].dt, [f[:2] for f in fields])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1.0)
+        e0.record(stream)
+        bat.step(args.batch_steps, ws[0].dt, fields)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tb = e0.elapsed_time(e1) * 1e-3
+        flush.fill_(1.0)
+        e0.record(stream)
+        for q, x in zip(props, ws):
+            q.step(args.batch_steps, x.dt, x.field)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts = e0.elapsed_time(e1) * 1e-3
+        batched = {"value": npts5 * args.batch_steps / tb, "unit": UNIT, "dtype": "f32",
+                   "workload": f"64 independent 2D Schroedinger lattices, sides from 256..2048 (radix 2 and 3), "
+                               f"{npts5} points in all, {args.batch_steps} lockstep split steps (sop_batch_step)",
+                   "one_plan_at_a_time": npts5 * args.batch_steps / ts}
+        # adjoint gradient of |<phi|psi_N>|^2 on one instance of that workload
+        x = ws[0]
+        q = props[0]
+        q.set_state(torch.from_numpy(x.psi0))
+        phi = torch.from_numpy(x.meta["phi"]).to(q.state.dtype).cuda()
+        gV = torch.zeros(x.psi0.shape, dtype=torch.float64, device="cuda")
+        q.adjoint_gradient(phi, 20, x.dt, x.field[:20], 20, gV)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q.adjoint_gradient(phi, args.batch_steps, x.dt, x.field, 20, gV)
+        torch.cuda.synchronize()
+        ta = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        q.step(args.batch_steps, x.dt, x.field)
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t0
+        adjoint = {"value": x.npoints * args.batch_steps / ta, "unit": UNIT, "dtype": "f32",
+                   "workload": f"J = |<phi|psi_N>|^2 and its gradient in all {args.batch_steps} field samples and "
+                               f"the potential grid, {x.dims[0]}x{x.dims[1]} lattice, checkpoints every 20 steps",
+                   "ratio_to_forward": ta / tf}
+        bat.close()
+        for q in props:
+            q.close()
+        torch.cuda.empty_cache()
+
     # ---- FP64 sample, same lattice -----------------------------------------
     fp64 = None
     if args.fp64_steps > 0:
@@ -364,7 +424,7 @@ def main():
                              "within a step",
                        "parallelism": f"replicas x{world} (independent problems, no data-path collective)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "fp64": fp64, "err_vs_oracle": err, "clocks": clocks,
+            "fp64": fp64, "batched": batched, "adjoint": adjoint, "err_vs_oracle": err, "clocks": clocks,
         }
         s = json.dumps(line)
         print(s, flush=True)
