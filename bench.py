@@ -55,8 +55,8 @@ def parse_args():
     ap.add_argument("--ref-split-steps", type=int, default=2, help="oracle split steps per reference step")
     ap.add_argument("--profile-every", type=int, default=64,
                     help="time the passes of one split step in this many (per-class roofline)")
-    ap.add_argument("--batched", type=int, default=1, help="also time the batched and adjoint forms (0: skip)")
-    ap.add_argument("--batch-steps", type=int, default=400, help="split steps of the batched / adjoint sample")
+    ap.add_argument("--batched", type=int, default=1, help="also time the batched, adjoint and spectral forms (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=400, help="split steps of the batched / adjoint / spectral sample")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
@@ -276,6 +276,7 @@ def main():
     # ---- batched and adjoint forms (the config-5 workload), complex64 -------
     batched = None
     adjoint = None
+    spectral = None
     if args.batched and rank == 0:
         ws = wl.config5(64, n_steps=args.batch_steps)
         npts5 = sum(x.npoints for x in ws)
@@ -329,6 +330,41 @@ def main():
         bat.close()
         for q in props:
             q.close()
+        torch.cuda.empty_cache()
+        # spectral method for eigenstates: 2D soft core (zeta = 0.791), trial
+        # Gaussian, chi_n every step, the windowed spectrum on 201 energies and
+        # the eigenfunctions at 4 of them
+        ns, hs = 2048, 0.2
+        Vs = wl.soft_core((ns, ns), (hs, hs), 0.791 ** 2)
+        psis = wl.gaussian((ns, ns), (hs, hs), (0.5, -0.3), 1.2)
+        q = sop.Propagator((ns, ns), (hs, hs), 1, "c64")
+        q.set_potential(Vs)
+        Es = np.linspace(-0.6, -0.4, 201)
+        q.set_state(torch.from_numpy(psis))
+        q.spectral(20, 0.05, Es[:4], True)
+        torch.cuda.synchronize()
+        q.set_state(torch.from_numpy(psis))
+        t0 = time.perf_counter()
+        q.spectral(args.batch_steps, 0.05, Es, False)
+        torch.cuda.synchronize()
+        tsp = time.perf_counter() - t0
+        q.set_state(torch.from_numpy(psis))
+        t0 = time.perf_counter()
+        _, _, psiE = q.spectral(args.batch_steps, 0.05, Es[:4], True)
+        torch.cuda.synchronize()
+        tse = time.perf_counter() - t0
+        del psiE
+        q.set_state(torch.from_numpy(psis))
+        t0 = time.perf_counter()
+        q.step(args.batch_steps, 0.05)
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t0
+        spectral = {"value": ns * ns * args.batch_steps / tse, "unit": UNIT, "dtype": "f32",
+                    "workload": f"spectral eigenstates: {ns}x{ns} 2D soft core (zeta 0.791), {args.batch_steps} "
+                                f"steps, chi every step, spectrum on 201 energies, eigenfunctions at 4",
+                    "spectrum_only": ns * ns * args.batch_steps / tsp,
+                    "ratio_to_forward": tse / tf}
+        q.close()
         torch.cuda.empty_cache()
 
     # ---- FP64 sample, same lattice -----------------------------------------
@@ -424,7 +460,7 @@ def main():
                              "within a step",
                        "parallelism": f"replicas x{world} (independent problems, no data-path collective)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "fp64": fp64, "batched": batched, "adjoint": adjoint, "err_vs_oracle": err, "clocks": clocks,
+            "fp64": fp64, "batched": batched, "adjoint": adjoint, "spectral": spectral, "err_vs_oracle": err, "clocks": clocks,
         }
         s = json.dumps(line)
         print(s, flush=True)

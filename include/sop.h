@@ -225,6 +225,37 @@ int sop_batch_create(sop_batch *out, int n_plans, const sop_plan *plans);
 int sop_batch_step(sop_batch batch, int64_t n_steps, double dt, const double *const *field_samples);
 int sop_batch_destroy(sop_batch batch);
 
+/* Spectral method for eigenstates (the paper's eigenstates subsection): the
+ * bound state is the trial state psi_0; it is advanced n_steps steps of size
+ * dt in the time-independent potential (no field; each step a complete
+ * Strang step, Eqs. 6-8 with the split of Eqs. 10a-b, so that every psi_n is
+ * in real space), leaving psi_N bound.  With t_n = n dt, T = N dt:
+ *   chi_n   = dV sum_j conj(psi_0,j) psi_n,j                 (autocorrelation)
+ *   chi~(E) = dt sum_n (1 - cos(2 pi t_n / T)) chi_n exp(i E t_n / hbar)
+ *   Psi_E   = dt sum_n (1 - cos(2 pi t_n / T)) psi_n exp(i E t_n / hbar)
+ * for n = 0..N (the window vanishes at both ends); peaks of |chi~| are the
+ * eigenvalues the trial state overlaps with and Psi_E at such a peak is the
+ * (unnormalised) eigenfunction.  Sums over j run over all components (the
+ * state's flat layout), so Dirac plans work alike.
+ *   chi_out       host, 2 (n_steps + 1) doubles (re, im pairs) or NULL;
+ *   energies      host, n_energies finite values (may be 0 with NULL);
+ *   spectrum_out  host, 2 n_energies doubles (chi~(E_k) pairs) or NULL;
+ *   psiE_dev      device complex128 [n_energies][points x components] in the
+ *                 state's layout, 16-byte aligned, or NULL; requires
+ *                 n_energies <= SOP_SPECTRAL_MAX_EIGEN.
+ * chi is summed to about 48 significant bits or more (products, and sums of
+ * four of them, in the state's precision; then float pairs for complex64
+ * states, FP64 for complex128 states; block sums in FP64).  Psi_E is accumulated from the states of up to 8 consecutive
+ * steps at a time (kept in a ring of state copies on the device; fewer when
+ * memory is short), in FP64 for complex128 states and as an unevaluated sum
+ * of two floats (about 48 significant bits) for complex64 states.  Synchronous (returns when the results are
+ * on the host).  Errors: SOP_EINVAL for bad arguments, SOP_ESTATE without a
+ * bound state, SOP_ENOMEM for the scratch (one state copy and
+ * 2 (n_steps + 1) doubles on the device). */
+#define SOP_SPECTRAL_MAX_EIGEN 16
+int sop_spectral(sop_plan plan, int64_t n_steps, double dt, int n_energies, const double *energies,
+                 double *chi_out, double *spectrum_out, void *psiE_dev);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *sop_last_error(void);
 

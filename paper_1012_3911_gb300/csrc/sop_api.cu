@@ -1391,4 +1391,124 @@ int sop_adjoint_gradient(sop_plan p, const void *phi_dev, int64_t n_steps, doubl
     return check_errflag(p);
 }
 
+int sop_spectral(sop_plan p, int64_t n_steps, double dt, int n_energies, const double *energies, double *chi_out,
+                 double *spectrum_out, void *psiE_dev) {
+    static_assert(SOP_SPECTRAL_MAX_EIGEN == SOP_SPECTRAL_MAX_ENERGIES, "eigenfunction slots");
+    if (!p) return fail(SOP_EINVAL, "sop_spectral: null plan");
+    if (!p->psi) return fail(SOP_ESTATE, "sop_spectral: no state bound (the trial state psi_0)");
+    if (n_steps < 1) return fail(SOP_EINVAL, "sop_spectral: n_steps must be >= 1");
+    if (!std::isfinite(dt) || dt == 0.0) return fail(SOP_EINVAL, "sop_spectral: dt must be finite and nonzero");
+    if (n_energies < 0 || (n_energies > 0 && !energies))
+        return fail(SOP_EINVAL, "sop_spectral: n_energies < 0 or energies is NULL");
+    for (int k = 0; k < n_energies; ++k)
+        if (!std::isfinite(energies[k])) return fail(SOP_EINVAL, "sop_spectral: non-finite energy");
+    if (psiE_dev && n_energies > SOP_SPECTRAL_MAX_EIGEN)
+        return fail(SOP_EINVAL, "sop_spectral: more than SOP_SPECTRAL_MAX_EIGEN eigenfunction energies");
+    if (psiE_dev && reinterpret_cast<uintptr_t>(psiE_dev) % 16 != 0)
+        return fail(SOP_EINVAL, "sop_spectral: psiE must be 16-byte aligned");
+    const int64_t N = n_steps;
+    const int64_t len = p->npts * p->comps;
+    const size_t sb = (size_t)len * p->csz;
+    const int K = n_energies;
+    const bool want_psi = psiE_dev && K > 0;
+    double dV = 1.0;
+    for (int a = 0; a < p->ndim; ++a) dV *= p->h[a];
+    char *psi0 = nullptr, *ring = nullptr;
+    double *chi = nullptr, *part = nullptr, *Ed = nullptr, *spec = nullptr;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(p->stream);
+        dfree(psi0);
+        dfree(ring);
+        dfree(chi);
+        dfree(part);
+        dfree(Ed);
+        dfree(spec);
+    };
+    int rc = dalloc(&psi0, sb, "spectral trial state");
+    if (!rc) rc = dalloc(&chi, (size_t)(N + 1) * 2 * sizeof(double), "spectral autocorrelation");
+    if (!rc) rc = dalloc(&part, (size_t)(inner_partials() + 1) * sizeof(double), "spectral partials");
+    if (!rc && K > 0) rc = dalloc(&Ed, (size_t)K * sizeof(double), "spectral energies");
+    if (!rc && K > 0) rc = dalloc(&spec, (size_t)K * 2 * sizeof(double), "spectral values");
+    if (rc) {
+        cleanup();
+        return rc;
+    }
+    // eigenfunctions: a ring of B states so that the K accumulators are read
+    // and written once per B steps; without room for it, B = 1 straight from psi
+    int B = 1;
+    if (want_psi)
+        for (int b = SOP_SPECTRAL_RING; b > 1 && !ring; b /= 2)
+            if (cudaMalloc(reinterpret_cast<void **>(&ring), (size_t)b * sb) == cudaSuccess)
+                B = b;
+            else {
+                ring = nullptr;
+                cudaGetLastError();   // clear the allocation error; try fewer slots
+            }
+    auto body = [&]() -> int {
+        // the block counter of the sample reduction sits after the partials
+        unsigned *done = reinterpret_cast<unsigned *>(part + inner_partials());
+        cudaError_t e = cudaMemcpyAsync(psi0, p->psi, sb, cudaMemcpyDeviceToDevice, p->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(done, 0, sizeof(unsigned), p->stream);
+        if (e == cudaSuccess && want_psi)
+            e = cudaMemsetAsync(psiE_dev, 0, (size_t)K * len * 2 * sizeof(double), p->stream);
+        if (e == cudaSuccess && K > 0)
+            e = cudaMemcpyAsync(Ed, energies, (size_t)K * sizeof(double), cudaMemcpyHostToDevice, p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "spectral set-up copies");
+        std::vector<double> wre((size_t)B * K), wim((size_t)B * K);
+        const double hbar = p->prm.hbar;
+        int fill = 0;
+        for (int64_t n = 0; n <= N; ++n) {
+            if (n > 0) {
+                const int r = step_impl(p, 1, dt, nullptr);
+                if (r) return r;
+            }
+            // the window 1 - cos(2 pi t_n / T) vanishes at n = 0 and n = N
+            const bool acc = want_psi && n > 0 && n < N;
+            e = launch_spectral_sample(psi0, p->psi, p->f64, len, acc && ring ? ring + (size_t)fill * sb : nullptr,
+                                       dV, part, done, chi + 2 * n, p->stream);
+            p->launches += 1;
+            if (e != cudaSuccess) return cuda_fail(e, "spectral sample");
+            if (!acc) continue;
+            const double t = (double)n * dt;
+            const double win = dt * (1.0 - std::cos(2.0 * M_PI * (double)n / (double)N));
+            for (int k = 0; k < K; ++k) {
+                const double ph = t * energies[k] / hbar;
+                wre[(size_t)fill * K + k] = win * std::cos(ph);
+                wim[(size_t)fill * K + k] = win * std::sin(ph);
+            }
+            if (++fill == B || n == N - 1) {
+                e = launch_spectral_accum(ring ? static_cast<const void *>(ring) : p->psi, p->f64, fill, len, K,
+                                          wre.data(), wim.data(), static_cast<double *>(psiE_dev), p->stream);
+                p->launches += 1;
+                if (e != cudaSuccess) return cuda_fail(e, "spectral accumulation");
+                fill = 0;
+            }
+        }
+        if (want_psi) {
+            e = launch_spectral_finish(static_cast<double *>(psiE_dev), p->f64, (int64_t)K * len, p->stream);
+            p->launches += p->f64 ? 0 : 1;
+            if (e != cudaSuccess) return cuda_fail(e, "spectral accumulator conversion");
+        }
+        if (K > 0) {
+            e = launch_spectrum(chi, N, dt, hbar, Ed, K, spec, p->stream);
+            p->launches += 1;
+            if (e != cudaSuccess) return cuda_fail(e, "spectral transform");
+        }
+        if (chi_out) {
+            e = cudaMemcpyAsync(chi_out, chi, (size_t)(N + 1) * 2 * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "spectral autocorrelation (D2H)");
+        }
+        if (spectrum_out && K > 0) {
+            e = cudaMemcpyAsync(spectrum_out, spec, (size_t)K * 2 * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "spectral values (D2H)");
+        }
+        e = cudaStreamSynchronize(p->stream);
+        return e == cudaSuccess ? SOP_OK : cuda_fail(e, "spectral results");
+    };
+    rc = body();
+    cleanup();
+    if (rc) return rc;
+    return check_errflag(p);
+}
+
 }  // extern "C"

@@ -130,6 +130,25 @@ cudaError_t launch_inner(const void *a, const void *b, bool f64, int ndim, const
 // acc[2j], acc[2j+1] += w conj(a_j) b_j
 cudaError_t launch_accum(const void *a, const void *b, bool f64, int64_t npts, double w, double *acc,
                          cudaStream_t s);
+// Spectral method.  launch_spectral_sample: chi[0..1] = dV <psi0|psi> and,
+// if slot is not NULL, a copy of psi into slot (len values); partial holds
+// inner_partials() doubles, *done is a zeroed counter (left zeroed).  launch_spectral_accum: acc[k][j] += sum_{b<B}
+// (wre[b K + k] + i wim[b K + k]) ring[b len + j] for B <= SOP_SPECTRAL_RING
+// states and K <= SOP_SPECTRAL_MAX_ENERGIES energies (acc: K x len double2).
+// For complex64 states the accumulator holds float pairs until
+// launch_spectral_finish (n = K x len values) turns them into complex128; a
+// no-op for complex128.
+// launch_spectrum: the windowed transform of chi (N + 1 pairs) at K energies
+// (device array E) into spec (2 K doubles).
+#define SOP_SPECTRAL_MAX_ENERGIES 16
+#define SOP_SPECTRAL_RING 8
+cudaError_t launch_spectral_sample(const void *psi0, const void *psi, bool f64, int64_t len, void *slot, double dV,
+                                   double *partial, unsigned *done, double *chi, cudaStream_t s);
+cudaError_t launch_spectral_accum(const void *ring, bool f64, int B, int64_t len, int K, const double *wre,
+                                  const double *wim, double *acc, cudaStream_t s);
+cudaError_t launch_spectral_finish(double *acc, bool f64, int64_t n, cudaStream_t s);
+cudaError_t launch_spectrum(const double *chi, int64_t N, double dt, double hbar, const double *E, int K,
+                            double *spec, cudaStream_t s);
 // g_j = 2 Re((zr + i zi) (acc[2j] + i acc[2j+1]))
 cudaError_t launch_grad_v(const double *acc, int64_t npts, double zr, double zi, double *g, cudaStream_t s);
 

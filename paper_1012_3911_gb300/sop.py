@@ -241,6 +241,33 @@ def sop_adjoint_gradient(plan: int, phi, n_steps: int, dt: float, field, every: 
     return J.value, g
 
 
+SOP_SPECTRAL_MAX_EIGEN = 16
+
+
+def sop_spectral(plan: int, n_steps: int, dt: float, energies=None, psiE=None):
+    """Spectral method from the bound (trial) state: returns (chi [n_steps+1],
+    spectrum [len(energies)]) as complex128 numpy arrays and, into the CUDA
+    complex128 tensor psiE of shape (len(energies), ...state shape) when given,
+    the eigenfunctions Psi_E; the bound state ends at psi_N.  See include/sop.h."""
+    lib = load()
+    fn = lib.sop_spectral
+    vp, d = ctypes.c_void_p, ctypes.c_double
+    fn.argtypes = [vp, ctypes.c_int64, d, ctypes.c_int, vp, vp, vp, vp]
+    fn.restype = ctypes.c_int
+    E = np.ascontiguousarray(np.atleast_1d(np.asarray([] if energies is None else energies, dtype=np.float64)))
+    chi = np.zeros(2 * (int(n_steps) + 1), dtype=np.float64)
+    spec = np.zeros(max(1, 2 * len(E)), dtype=np.float64)
+    pp = None
+    if psiE is not None:
+        import torch
+        if not psiE.is_cuda or not psiE.is_contiguous() or psiE.dtype != torch.complex128:
+            raise ValueError("psiE must be a contiguous complex128 CUDA tensor")
+        pp = psiE.data_ptr()
+    _check(fn(plan, int(n_steps), float(dt), len(E), E.ctypes.data if len(E) else None, chi.ctypes.data,
+              spec.ctypes.data, pp))
+    return chi.view(np.complex128), spec[:2 * len(E)].view(np.complex128)
+
+
 def sop_batch_create(plans) -> int:
     """A batch over plan handles (two-dimensional Schroedinger, one dtype and stream)."""
     lib = load()
@@ -359,6 +386,17 @@ class Propagator:
         import torch
         phi_t = torch.as_tensor(phi).to(self.state.device, self.state.dtype).contiguous()
         return sop_adjoint_gradient(self.plan, phi_t, n_steps, dt, field, every, self.ndim, grad_V)
+
+    def spectral(self, n_steps: int, dt: float, energies=None, eigenfunctions: bool = False):
+        """chi, spectrum (numpy complex128) and, with eigenfunctions=True, a
+        CUDA complex128 tensor of Psi_E per energy; the state ends at psi_N."""
+        import torch
+        psiE = None
+        if eigenfunctions:
+            n = len(np.atleast_1d(energies))
+            psiE = torch.zeros((n,) + tuple(self.state.shape), dtype=torch.complex128, device=self.state.device)
+        chi, spec = sop_spectral(self.plan, n_steps, dt, energies, psiE)
+        return chi, spec, psiE
 
     def close(self) -> None:
         if getattr(self, "plan", None):
