@@ -67,6 +67,9 @@ def _load():
         lib.orc_schr_propagate.argtypes = [P, P, ctypes.c_int, i64p, dp, d, d, d, d,
                                            ctypes.c_int64, P]
         lib.orc_schr_propagate.restype = ctypes.c_int
+        lib.orc_schr_propagate_gauge.argtypes = [P, P, ctypes.c_int, i64p, dp, d, d, d, d,
+                                                 ctypes.c_int64, P, ctypes.c_int]
+        lib.orc_schr_propagate_gauge.restype = ctypes.c_int
         lib.orc_dirac_propagate.argtypes = [P, P, ctypes.c_int, i64p, dp, d, d, d, d, d,
                                             ctypes.c_int64, P]
         lib.orc_dirac_propagate.restype = ctypes.c_int
@@ -176,13 +179,14 @@ def fftn(x, sign: int = -1) -> np.ndarray:
 
 def schrodinger_propagate(psi, V, spacing, dt: float, n_steps: int, field=None,
                           mass: float = 1.0, charge: float = -1.0,
-                          hbar: float = 1.0) -> np.ndarray:
+                          hbar: float = 1.0, gauge: str = "length") -> np.ndarray:
     """``n_steps`` Strang steps of Eq. 8 with the Schroedinger split of
-    Eqs. 10a/10b (length-gauge field).  ``psi`` has shape (…, ny, nx); ``V``
-    the same spatial shape (potential energy) or None; ``spacing`` is
-    (h_x, h_y, h_z) in axis order; ``field`` is (n_steps, ndim) electric-field
-    samples at step midpoints, components in axis order, or None.
-    Returns the propagated copy."""
+    Eqs. 10a/10b.  ``psi`` has shape (…, ny, nx); ``V`` the same spatial
+    shape (potential energy) or None; ``spacing`` is (h_x, h_y, h_z) in axis
+    order; ``field`` is (n_steps, ndim) samples at step midpoints, components
+    in axis order, or None: the electric field E (``gauge="length"``, in the
+    real-space factor) or the vector potential A (``gauge="velocity"``, in the
+    momentum-space factor of Eq. 13).  Returns the propagated copy."""
     y = _c128(psi).copy()
     ndim = y.ndim
     Vp = None
@@ -195,8 +199,11 @@ def schrodinger_propagate(psi, V, spacing, dt: float, n_steps: int, field=None,
     if field is not None:
         fc = _f64(field).reshape(int(n_steps), ndim)
         fp = fc.ctypes.data
-    rc = _load().orc_schr_propagate(y.ctypes.data, Vp, ndim, _dims(y.shape), _dp(spacing),
-                                    mass, charge, hbar, float(dt), int(n_steps), fp)
+    if gauge not in ("length", "velocity"):
+        raise ValueError("gauge must be 'length' or 'velocity'")
+    rc = _load().orc_schr_propagate_gauge(y.ctypes.data, Vp, ndim, _dims(y.shape), _dp(spacing),
+                                          mass, charge, hbar, float(dt), int(n_steps), fp,
+                                          0 if gauge == "length" else 1)
     if rc != 0:
         raise ValueError("unsupported shape")
     return y

@@ -242,11 +242,14 @@ static void schr_real_space(cplx *psi, const double *V, int ndim, const int64_t 
     }
 }
 
-/* Momentum-space factor U~_A2(t+tau, t, 1), Eq. 13 with Eq. 10b and A = 0
- * (the field is in the length gauge):
- *   psi~_k <- exp(-i tau |p_k|^2 / (2 m hbar)) psi~_k                     */
+/* Momentum-space factor U~_A2(t+tau, t, 1), Eq. 13 with Eq. 10b.  A = NULL
+ * (length gauge, or no field):
+ *   psi~_k <- exp(-i tau |p_k|^2 / (2 m hbar)) psi~_k
+ * Velocity gauge, A = the vector potential of this step (its midpoint value,
+ * so that the time integral of Eq. 13 is tau times the integrand there):
+ *   psi~_k <- exp(-i tau |p_k - q A|^2 / (2 m hbar)) psi~_k              */
 static void schr_momentum_space(cplx *psit, int ndim, const int64_t *dims, const double *h,
-                                double mass, double hbar, double tau) {
+                                double mass, double charge, double hbar, double tau, const double *A) {
     const int64_t N = npoints(ndim, dims);
 #pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int64_t k = 0; k < N; ++k) {
@@ -255,6 +258,7 @@ static void schr_momentum_space(cplx *psit, int ndim, const int64_t *dims, const
         double p2 = 0.0;
         for (int a = 0; a < ndim; ++a) {
             double p = lattice_p(dims[a], h[a], idx[a], hbar);
+            if (A) p -= charge * A[a];
             p2 += p * p;
         }
         double ang = -tau * p2 / (2.0 * mass * hbar);
@@ -262,23 +266,33 @@ static void schr_momentum_space(cplx *psit, int ndim, const int64_t *dims, const
     }
 }
 
-/* n_steps Strang steps (Eq. 8).  field: n_steps x ndim electric-field
- * samples (midpoint of each step) or NULL. */
-int orc_schr_propagate(cplx *psi, const double *V, int ndim, const int64_t *dims,
-                       const double *h, double mass, double charge, double hbar, double tau,
-                       int64_t n_steps, const double *field) {
-    if (ndim < 1 || ndim > 3) return -1;
+/* n_steps Strang steps (Eq. 8).  field: n_steps x ndim samples (midpoint
+ * of each step) or NULL; gauge 0: electric field E in the real-space factor
+ * (length gauge, Eq. 11 with q phi = V - q x.E); gauge 1: vector potential A
+ * in the momentum-space factor (velocity gauge, Eq. 13). */
+int orc_schr_propagate_gauge(cplx *psi, const double *V, int ndim, const int64_t *dims,
+                             const double *h, double mass, double charge, double hbar, double tau,
+                             int64_t n_steps, const double *field, int gauge) {
+    if (ndim < 1 || ndim > 3 || gauge < 0 || gauge > 1) return -1;
     for (int a = 0; a < ndim; ++a)
         if (!orc_size_ok(dims[a])) return -1;
     for (int64_t n = 0; n < n_steps; ++n) {
-        const double *E = field ? field + n * ndim : NULL;
+        const double *F = field ? field + n * ndim : NULL;
+        const double *E = gauge == 0 ? F : NULL;
+        const double *A = gauge == 1 ? F : NULL;
         schr_real_space(psi, V, ndim, dims, h, charge, hbar, tau, 0.5, E);
         orc_fftn(psi, ndim, dims, -1);
-        schr_momentum_space(psi, ndim, dims, h, mass, hbar, tau);
+        schr_momentum_space(psi, ndim, dims, h, mass, charge, hbar, tau, A);
         orc_fftn(psi, ndim, dims, +1);
         schr_real_space(psi, V, ndim, dims, h, charge, hbar, tau, 0.5, E);
     }
     return 0;
+}
+
+int orc_schr_propagate(cplx *psi, const double *V, int ndim, const int64_t *dims,
+                       const double *h, double mass, double charge, double hbar, double tau,
+                       int64_t n_steps, const double *field) {
+    return orc_schr_propagate_gauge(psi, V, ndim, dims, h, mass, charge, hbar, tau, n_steps, field, 0);
 }
 
 /* ------------------------------------------------------------------ */

@@ -33,6 +33,10 @@ MUTANTS = [
      [pins.pin_coherent_state_second_order, pins.pin_constant_potential_phase]),
     ("field_sign", "W -= charge * lattice_x(dims[a], h[a], idx[a]) * E[a];",
      "W += charge * lattice_x(dims[a], h[a], idx[a]) * E[a];", [pins.pin_field_kick_plane_wave]),
+    ("velocity_gauge_sign", "if (A) p -= charge * A[a];", "if (A) p += charge * A[a];",
+     [pins.pin_velocity_gauge_plane_waves, pins.pin_velocity_gauge_lattice_shift]),
+    ("velocity_gauge_drops_A", "if (A) p -= charge * A[a];", "(void)A;",
+     [pins.pin_velocity_gauge_plane_waves, pins.pin_velocity_gauge_lattice_shift]),
     ("lattice_origin", "return -0.5 * (double)n * h + (double)j * h;",
      "return -0.5 * (double)n * h + (double)(j + 1) * h;", [pins.pin_field_kick_plane_wave]),
     ("dirac_u_not_adjoint", "for (int k = 0; k < 4; ++k) s += conj(u[k][i]) * w[k];",
