@@ -23,9 +23,10 @@
  *     points.  dims[0] = n_x.
  *   - Fields: field_samples holds n_steps rows of ndim doubles, the field at
  *     the midpoint t_n + tau/2 of each step, components in axis order.  For
- *     Schroedinger it is the electric field E in the length gauge (the scalar
- *     potential gains -q x.E); for Dirac it is the uniform vector potential A
- *     of Eq. 18a.  NULL means no field.
+ *     Schroedinger it is by default the electric field E in the length gauge
+ *     (the scalar potential gains -q x.E), or the vector potential A in the
+ *     velocity gauge after sop_set_gauge; for Dirac it is the uniform vector
+ *     potential A of Eq. 18a.  NULL means no field.
  *   - Every call returns a sop_status.  Nothing throws across the ABI.  On a
  *     non-zero status, sop_last_error() returns a thread-local message.
  *   - Ownership: the plan owns its tables and scratch (device memory it
@@ -102,6 +103,20 @@ int sop_bind_state(sop_plan plan, void *psi_dev);
  * exp(-i V tau/(2 hbar)) and exp(-i V tau/hbar) at the next sop_step.
  * A plan whose potential was never set uses V = 0. */
 int sop_set_potential(sop_plan plan, const void *V_dev, int v_is_fp64);
+
+/* Meaning of the field samples of a Schroedinger plan (Sec. 2.2):
+ * SOP_GAUGE_LENGTH (the default): field_samples are the electric field E
+ * at each step's midpoint, entering the real-space factor (Eq. 11 with
+ * q phi = V - q x.E, the length gauge).  SOP_GAUGE_VELOCITY: they are the
+ * vector potential A at each step's midpoint, entering the momentum-space
+ * factor of Eq. 13 as exp(-i tau |p - q A|^2 / (2 m hbar)) (the time integral
+ * of Eq. 13 by the midpoint rule; per-step kinetic rows are built on the
+ * device for every 512 steps).  Dirac plans always take A (SOP_EUNSUPPORTED
+ * here).  The adjoint gradient and batches accept length-gauge plans only.
+ * Returns SOP_EINVAL for another value. */
+#define SOP_GAUGE_LENGTH 0
+#define SOP_GAUGE_VELOCITY 1
+int sop_set_gauge(sop_plan plan, int gauge);
 
 /* Advance the bound state by n_steps Strang steps of size dt (Eq. 8).  The
  * real-space factors of adjacent steps are merged (exact algebra): the call

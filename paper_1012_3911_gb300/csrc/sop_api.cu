@@ -84,6 +84,7 @@ struct sop_plan_s {
     bool tables_valid = false;
     double scale_hi = 1.0, scale_lo = 0.0;
 
+    int gauge = SOP_GAUGE_LENGTH;   // meaning of the Schroedinger field samples
     void *ftab = nullptr;           // kFieldChunk rows x row_len
     int64_t row_len = 0;
     int64_t foff[3] = {0, 0, 0};
@@ -492,10 +493,12 @@ struct FieldRows {
     int64_t row_len = 0;
 };
 
-// Field vectors of the real-space factors of n steps, f_P = -q tau/(2 hbar)
+// Field vectors of n steps, uploaded to p->fvec and turned into rows per
+// chunk.  Length gauge: the real-space factors' f_P = -q tau/(2 hbar)
 // (E_{P-1} + E_P) for P = 0..n (the laser part of exp(-i tau W/(2 hbar)) of
-// both adjacent half steps), uploaded to p->fvec; the rows are built per
-// chunk by build_field_tables.
+// both adjacent half steps; build_field_tables).  Velocity gauge: the
+// kinetic factors' momentum shifts s_P = q A_P for P = 0..n-1
+// (build_kin_field_tables).
 int prepare_fields(sop_plan p, int64_t n, double dt, const double *field, FieldRows &fr) {
     const int nd = p->ndim;
     auto sample = [&](int64_t s, int a) -> double {
@@ -517,9 +520,15 @@ int prepare_fields(sop_plan p, int64_t n, double dt, const double *field, FieldR
             p->fvec_cap = (n + 1) * nd;
         }
         std::vector<double> fv((size_t)(n + 1) * nd);
-        const double k = -p->prm.charge * dt / (2.0 * p->prm.hbar);
-        for (int64_t P = 0; P <= n; ++P)
-            for (int a = 0; a < nd; ++a) fv[P * nd + a] = k * (sample(P - 1, a) + sample(P, a));
+        if (p->gauge == SOP_GAUGE_VELOCITY) {
+            // momentum shifts s_P = q A_P of the kinetic factors, P = 0..n-1
+            for (int64_t P = 0; P <= n; ++P)
+                for (int a = 0; a < nd; ++a) fv[P * nd + a] = p->prm.charge * sample(P, a);
+        } else {
+            const double k = -p->prm.charge * dt / (2.0 * p->prm.hbar);
+            for (int64_t P = 0; P <= n; ++P)
+                for (int a = 0; a < nd; ++a) fv[P * nd + a] = k * (sample(P - 1, a) + sample(P, a));
+        }
         int rc = upload(p, p->fvec, fv.data(), (int64_t)fv.size());
         if (rc) return rc;
     }
@@ -599,17 +608,29 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
     const int64_t *offs = fr.offs;
     const int64_t row_len = fr.row_len;
 
+    // the field enters the real-space factors (length gauge) or the kinetic
+    // factors (velocity gauge)
+    const bool vel = p->gauge == SOP_GAUGE_VELOCITY;
+    const bool rfield = any_field && !vel, kfield = any_field && vel;
     for (int64_t P0 = 0; P0 <= n; P0 += kFieldChunk) {
         const int64_t P1 = std::min<int64_t>(n + 1, P0 + kFieldChunk);
         if (any_field) {
             Bracket br(p, 4);
-            cudaError_t e = build_field_tables(p->ftab, p->fvec + P0 * nd, P1 - P0, nd, p->dims, p->h, active, offs,
-                                               row_len, p->f64, p->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "build_field_tables");
+            cudaError_t e = vel ? build_kin_field_tables(p->ftab, p->fvec + P0 * nd, std::min(P1, n) - P0, nd, p->dims,
+                                                         p->h, active, offs, row_len,
+                                                         dt / (2.0 * p->prm.mass * p->prm.hbar), p->prm.hbar, p->f64,
+                                                         p->stream)
+                                : build_field_tables(p->ftab, p->fvec + P0 * nd, P1 - P0, nd, p->dims, p->h, active,
+                                                     offs, row_len, p->f64, p->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "field tables");
             br.done();
         }
         auto frow = [&](int64_t P, int a) -> const void * {
-            if (!active[a]) return nullptr;
+            if (!rfield || !active[a]) return nullptr;
+            return static_cast<const char *>(p->ftab) + ((P - P0) * row_len + offs[a]) * p->csz;
+        };
+        auto krow = [&](int64_t P, int a) -> const void * {
+            if (!kfield || !active[a]) return p->kin[a];
             return static_cast<const char *>(p->ftab) + ((P - P0) * row_len + offs[a]) * p->csz;
         };
         if (nd == 1) {
@@ -623,8 +644,9 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
             a1.tw = p->tw[0];
             a1.vhalf = p->v_set ? p->vhalf : nullptr;
             a1.vfull = p->v_set ? p->vfull : nullptr;
-            a1.ftab = any_field ? p->ftab : nullptr;
-            a1.ttab = p->kin[0];
+            a1.ftab = rfield ? p->ftab : nullptr;
+            a1.ttab = kfield ? p->ftab : p->kin[0];
+            a1.ttab_stride = kfield ? row_len : 0;
             a1.scale_hi = p->scale_hi;
             a1.scale_lo = p->scale_lo;
             Bracket br(p, 3);
@@ -652,7 +674,7 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
                 k.pre = -1;
                 k.post = +1;
                 k.op = OP_T;
-                for (int ax = 0; ax < nd; ++ax) k.ttab[ax] = p->kin[ax];
+                for (int ax = 0; ax < nd; ++ax) k.ttab[ax] = krow(P, ax);
                 rc = run_pass(p, k, 1, 1, "momentum-space pass", smp);
                 if (rc) return rc;
             } else {
@@ -667,7 +689,7 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
                 k.pre = -1;
                 k.post = +1;
                 k.op = OP_T;
-                for (int ax = 0; ax < nd; ++ax) k.ttab[ax] = p->kin[ax];
+                for (int ax = 0; ax < nd; ++ax) k.ttab[ax] = krow(P, ax);
                 rc = run_pass(p, k, 1, 1, "momentum-space pass", smp);
                 if (rc) return rc;
                 y.pre = +1;
@@ -868,6 +890,15 @@ int sop_set_potential(sop_plan p, const void *V_dev, int v_is_fp64) {
     return SOP_OK;
 }
 
+int sop_set_gauge(sop_plan p, int gauge) {
+    if (!p) return fail(SOP_EINVAL, "sop_set_gauge: null plan");
+    if (gauge != SOP_GAUGE_LENGTH && gauge != SOP_GAUGE_VELOCITY)
+        return fail(SOP_EINVAL, "sop_set_gauge: gauge must be SOP_GAUGE_LENGTH or SOP_GAUGE_VELOCITY");
+    if (p->comps != 1) return fail(SOP_EUNSUPPORTED, "sop_set_gauge: Schroedinger plans only (Dirac takes A)");
+    p->gauge = gauge;
+    return SOP_OK;
+}
+
 int sop_step(sop_plan p, int64_t n_steps, double dt, const double *field_samples) {
     return step_impl(p, n_steps, dt, field_samples);
 }
@@ -1034,6 +1065,7 @@ int sop_batch_create(sop_batch *out, int n_plans, const sop_plan *plans) {
         if (!p) return fail(SOP_EINVAL, "sop_batch_create: null plan");
         if (p->comps != 1 || p->ndim != 2)
             return fail(SOP_EUNSUPPORTED, "sop_batch_create: two-dimensional Schroedinger plans only");
+        if (p->gauge != SOP_GAUGE_LENGTH) return fail(SOP_EUNSUPPORTED, "sop_batch_create: length-gauge plans only");
         if (p->f64 != plans[0]->f64 || p->stream != plans[0]->stream)
             return fail(SOP_EINVAL, "sop_batch_create: plans differ in dtype or stream");
 
@@ -1069,6 +1101,7 @@ int sop_batch_step(sop_batch b, int64_t n, double dt, const double *const *field
     for (int i = 0; i < np; ++i) {
         sop_plan p = b->plans[i];
         if (!p->psi) return fail(SOP_ESTATE, "sop_batch_step: a plan has no state bound");
+        if (p->gauge != SOP_GAUGE_LENGTH) return fail(SOP_EUNSUPPORTED, "sop_batch_step: length-gauge plans only");
         const double *f = fields ? fields[i] : nullptr;
         if (f)
             for (int64_t k = 0; k < n * 2; ++k)
@@ -1238,6 +1271,8 @@ int sop_adjoint_gradient(sop_plan p, const void *phi_dev, int64_t n_steps, doubl
                          int64_t every, double *J, double *grad_field, double *grad_V_dev) {
     if (!p) return fail(SOP_EINVAL, "sop_adjoint_gradient: null plan");
     if (p->comps != 1) return fail(SOP_EUNSUPPORTED, "sop_adjoint_gradient: Schroedinger plans only");
+    if (p->gauge != SOP_GAUGE_LENGTH)
+        return fail(SOP_EUNSUPPORTED, "sop_adjoint_gradient: length-gauge plans only");
     if (!p->psi) return fail(SOP_ESTATE, "sop_adjoint_gradient: no state bound (psi_0)");
     if (!phi_dev || !J) return fail(SOP_EINVAL, "sop_adjoint_gradient: phi or J is NULL");
     if (n_steps < 1 || every < 1) return fail(SOP_EINVAL, "sop_adjoint_gradient: n_steps and every must be >= 1");

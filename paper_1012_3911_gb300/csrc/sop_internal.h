@@ -95,7 +95,8 @@ struct Args1D {
     const void *tw;
     const void *vhalf, *vfull;   // phase tables (may be null)
     const void *ftab;            // field tables, row per real-space index, n entries (may be null)
-    const void *ttab;            // kinetic table
+    const void *ttab;            // kinetic table, or rows of ttab_stride entries per step (velocity gauge)
+    int64_t ttab_stride;         // 0: one table for every step; else row (P - p_table0) for step P
     double scale_hi, scale_lo;
 };
 
@@ -178,6 +179,11 @@ cudaError_t build_twiddles(void *out, int n, bool f64, cudaStream_t s);
 cudaError_t build_vphase(void *out, const double *V, int64_t npts, double factor, bool f64,
                          cudaStream_t s);
 cudaError_t build_axis_phase(void *out, const double *coef, int n, bool f64, cudaStream_t s);
+// Velocity-gauge kinetic rows (Eq. 13): row P (< n_rows) holds, for each
+// active axis a at offsets[a], exp(-i c (p_{a,k} - svec[P ndim + a])^2).
+cudaError_t build_kin_field_tables(void *out, const double *svec, int64_t n_rows, int ndim, const int64_t *dims,
+                                   const double *spacing, const int *active, const int64_t *offsets, int64_t row_len,
+                                   double c, double hbar, bool f64, cudaStream_t s);
 cudaError_t build_field_tables(void *out, const double *fvec, int64_t n_rows, int ndim,
                                const int64_t *dims, const double *spacing, const int *active,
                                const int64_t *offsets, int64_t row_len, bool f64, cudaStream_t s);

@@ -318,8 +318,9 @@ __global__ void __launch_bounds__(Geometry<N, 1>::T) fso1d_kernel(const __grid_c
         }
         if (P < a.n_steps) {
             fft_forward<C, N, E, 1>(v, lay, t, tw);
+            const C *tr = tt + (P - a.p_table0) * a.ttab_stride;
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[0][m] = scale2(Ph::apply(v[0][m], ldg_c(tt + t + T * m)), shi, slo);
+            for (int m = 0; m < E; ++m) v[0][m] = scale2(Ph::apply(v[0][m], ldg_c(tr + t + T * m)), shi, slo);
             __syncthreads();
             fft_dir<C, N, E, 1>(v, lay, t, tw, +1);
             __syncthreads();

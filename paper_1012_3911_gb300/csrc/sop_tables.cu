@@ -94,6 +94,23 @@ __global__ void k_field(void *out, const double *fvec, int64_t n_rows, int64_t r
     }
 }
 
+// Velocity gauge (Eq. 13 with the vector potential): row P, axis a, index k:
+// exp(-i c (p_{a,k} - s_{P,a})^2) with s_P = q A_P and c = tau / (2 m hbar).
+__global__ void k_kin_field(void *out, const double *svec, int64_t n_rows, int64_t row_len, FieldGeom g, double c,
+                            double hbar, bool f64) {
+    const int64_t total = n_rows * row_len;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t P = idx / row_len;
+        const int64_t r = idx - P * row_len;
+        int a = 0;
+        while (a + 1 < g.ndim && (!g.active[a] || r >= g.offsets[a] + g.dims[a])) ++a;
+        const int64_t k = r - g.offsets[a];
+        const double d = lattice_p(g.dims[a], g.spacing[a], k, hbar) - svec[P * g.ndim + a];
+        store_phase(out, idx, c * d * d, f64);
+    }
+}
+
 // Dirac momentum-space factor (Eq. 33) in closed form per momentum:
 //   U = cos(E tau/hbar) - i sin(E tau/hbar) H(p)/E,  H = c alpha.p + m c^2 beta,
 // stored as (cos, sin*mc^2/E, sin*c p_x/E, sin*c p_y/E).
@@ -162,6 +179,22 @@ cudaError_t build_field_tables(void *out, const double *fvec, int64_t n_rows, in
         g.offsets[a] = a < ndim ? offsets[a] : 0;
     }
     k_field<<<grid_for(n_rows * row_len, 256), 256, 0, s>>>(out, fvec, n_rows, row_len, g, f64);
+    return cudaGetLastError();
+}
+
+cudaError_t build_kin_field_tables(void *out, const double *svec, int64_t n_rows, int ndim, const int64_t *dims,
+                                   const double *spacing, const int *active, const int64_t *offsets, int64_t row_len,
+                                   double c, double hbar, bool f64, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    FieldGeom g{};
+    g.ndim = ndim;
+    for (int a = 0; a < 3; ++a) {
+        g.dims[a] = a < ndim ? dims[a] : 1;
+        g.spacing[a] = a < ndim ? spacing[a] : 1.0;
+        g.active[a] = a < ndim ? active[a] : 0;
+        g.offsets[a] = a < ndim ? offsets[a] : 0;
+    }
+    k_kin_field<<<grid_for(n_rows * row_len, 256), 256, 0, s>>>(out, svec, n_rows, row_len, g, c, hbar, f64);
     return cudaGetLastError();
 }
 

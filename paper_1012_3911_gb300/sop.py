@@ -241,6 +241,19 @@ def sop_adjoint_gradient(plan: int, phi, n_steps: int, dt: float, field, every: 
     return J.value, g
 
 
+SOP_GAUGE_LENGTH = 0
+SOP_GAUGE_VELOCITY = 1
+
+
+def sop_set_gauge(plan: int, gauge: int) -> None:
+    """Field samples of a Schroedinger plan: E (length gauge, the default) or
+    A (velocity gauge, Eq. 13)."""
+    lib = load()
+    lib.sop_set_gauge.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.sop_set_gauge.restype = ctypes.c_int
+    _check(lib.sop_set_gauge(plan, int(gauge)))
+
+
 SOP_SPECTRAL_MAX_EIGEN = 16
 
 
@@ -367,6 +380,12 @@ class Propagator:
         if Vt.dtype not in (torch.float32, torch.float64):
             Vt = Vt.double()
         sop_set_potential(self.plan, Vt.to(self.state.device).contiguous())
+
+    def set_gauge(self, gauge: str) -> None:
+        """"length" (field samples are E) or "velocity" (field samples are A)."""
+        if gauge not in ("length", "velocity"):
+            raise ValueError("gauge must be 'length' or 'velocity'")
+        sop_set_gauge(self.plan, SOP_GAUGE_LENGTH if gauge == "length" else SOP_GAUGE_VELOCITY)
 
     def step(self, n_steps: int, dt: float, field=None) -> None:
         sop_step(self.plan, n_steps, dt, field, self.ndim)
