@@ -277,6 +277,7 @@ def main():
     batched = None
     adjoint = None
     spectral = None
+    velocity = None
     if args.batched and rank == 0:
         ws = wl.config5(64, n_steps=args.batch_steps)
         npts5 = sum(x.npoints for x in ws)
@@ -365,6 +366,28 @@ def main():
                     "spectrum_only": ns * ns * args.batch_steps / tsp,
                     "ratio_to_forward": tse / tf}
         q.close()
+        torch.cuda.empty_cache()
+        # velocity gauge on the benchmark lattice: A = -integral of E (so that
+        # E = -dA/dt), the same split steps with per-step kinetic rows
+        qv = sop.Propagator(w.dims, w.spacing, 1, "c64")
+        qv.set_gauge("velocity")
+        qv.set_potential(w.V)
+        Avel = -np.cumsum(w.field, axis=0) * w.dt
+        qv.state.copy_(psi0)
+        qv.step(4, w.dt, Avel[:4])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        qv.state.copy_(psi0)
+        flush.fill_(1.0)
+        e0.record(stream)
+        qv.step(S, w.dt, Avel)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tv = e0.elapsed_time(e1) * 1e-3
+        velocity = {"value": w.npoints * S / tv, "unit": UNIT, "dtype": "f32",
+                    "workload": f"benchmark lattice and potential, vector potential A = -int E dt in the "
+                                f"momentum-space factor (Eq. 13), {S} split steps",
+                    "ratio_to_length_gauge": tv / (total_ms * 1e-3 / args.steps)}
+        qv.close()
         torch.cuda.empty_cache()
 
     # ---- FP64 sample, same lattice -----------------------------------------
@@ -460,7 +483,7 @@ def main():
                              "within a step",
                        "parallelism": f"replicas x{world} (independent problems, no data-path collective)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "fp64": fp64, "batched": batched, "adjoint": adjoint, "spectral": spectral, "err_vs_oracle": err, "clocks": clocks,
+            "fp64": fp64, "batched": batched, "adjoint": adjoint, "spectral": spectral, "velocity_gauge": velocity, "err_vs_oracle": err, "clocks": clocks,
         }
         s = json.dumps(line)
         print(s, flush=True)

@@ -4,8 +4,14 @@
 
 runs ``sop_step`` on the seeded workload of the given configuration (1: 1D
 harmonic, 2: 2D laser-driven soft core, 3: 3D, 4: 2D Dirac), in the listed
-chunks of steps, and prints norm and energy after each chunk.  Used as a
-small driver for profilers as well.
+chunks of steps, and prints norm and energy after each chunk.
+
+    python -m paper_1012_3911_gb300.run --spectral 4 --n 2048 --steps 24
+
+runs ``sop_spectral`` instead: a Gaussian trial state in the 2D soft-core
+well of the eigenstates subsection (zeta = 0.791, spacing 0.2, dt = 0.05) for
+the given number of steps, the spectrum and the eigenfunctions at that many
+energies in [-0.6, -0.4].  Used as a small driver for profilers as well.
 """
 from __future__ import annotations
 
@@ -20,14 +26,33 @@ def main(argv=None):
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--steps", default="3,2", help="comma-separated chunks of split steps")
     ap.add_argument("--no-energy", action="store_true")
+    ap.add_argument("--spectral", type=int, default=0,
+                    help="run the spectral method with eigenfunctions at this many energies (<= 16)")
     args = ap.parse_args(argv)
 
+    import numpy as np
     import torch
     from . import build, workloads as wl
     from .sop import Propagator
 
     build.build()
     chunks = [int(s) for s in args.steps.split(",") if s]
+    if args.spectral:
+        n, h = args.n or 2048, 0.2
+        steps = max(1, sum(chunks))
+        p = Propagator((n, n), (h, h), 1, args.dtype)
+        p.set_state(torch.from_numpy(wl.gaussian((n, n), (h, h), (0.5, -0.3), 1.2)))
+        p.set_potential(wl.soft_core((n, n), (h, h), 0.791 ** 2))
+        E = np.linspace(-0.6, -0.4, args.spectral)
+        t0 = time.perf_counter()
+        chi, spec, _ = p.spectral(steps, 0.05, E, True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        k = int(np.argmax(np.abs(spec)))
+        print(f"spectral {n}x{n} {args.dtype}: {steps} steps in {dt * 1e3:.2f} ms, |chi_N| {abs(chi[-1]):.9f}, "
+              f"largest |spectrum| at E = {E[k]:.4f}", flush=True)
+        p.close()
+        return
     kw = {} if args.n is None else {"n": args.n}
     w = wl.CONFIGS[args.config](n_steps=max(1, sum(chunks)), **kw)
     p = Propagator(w.dims, w.spacing, w.comps, args.dtype)
