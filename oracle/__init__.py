@@ -75,6 +75,10 @@ def _load():
         lib.orc_dirac_propagate.restype = ctypes.c_int
         lib.orc_dirac_alpha_beta.argtypes = [P]
         lib.orc_dirac_u.argtypes = [dp, ctypes.c_int, d, d, P]
+        lib.orc_dirac1d_u.argtypes = [d, d, d, P]
+        lib.orc_dirac1d_h.argtypes = [d, d, d, P]
+        lib.orc_dirac1d_propagate.argtypes = [P, P, ctypes.c_int64, d, d, d, d, d, d, ctypes.c_int64, P]
+        lib.orc_dirac1d_propagate.restype = ctypes.c_int
         lib.orc_dirac_h.argtypes = [dp, ctypes.c_int, d, d, P]
         lib.orc_dirac_kinetic_matrix.argtypes = [dp, ctypes.c_int, d, d, d, d, P]
         lib.orc_dirac_mixing_matrix.argtypes = [dp, ctypes.c_int, d, d, d, d, d, P]
@@ -238,6 +242,49 @@ def dirac_propagate(psi, V, spacing, dt: float, n_steps: int, field=None,
     return y
 
 
+def dirac1d_propagate(psi, V, spacing, dt: float, n_steps: int, field=None,
+                      mass: float = 1.0, charge: float = -1.0, hbar: float = 1.0,
+                      c: float = 137.036) -> np.ndarray:
+    """``n_steps`` Strang steps of the one-dimensional two-component Dirac
+    equation (end of Sec. 2.3; alpha_1 = sigma_x, beta = sigma_z) for a spinor
+    of shape (2, n).  ``field`` holds vector-potential samples A_1 (n_steps,)
+    at step midpoints, or None.  Returns the propagated copy."""
+    y = _c128(psi).copy()
+    if y.ndim != 2 or y.shape[0] != 2:
+        raise ValueError("1D Dirac spinor needs shape (2, n)")
+    n = y.shape[1]
+    Vp = None
+    if V is not None:
+        Vc = _f64(V)
+        if Vc.shape != (n,):
+            raise ValueError("V must have shape (n,)")
+        Vp = Vc.ctypes.data
+    fp = None
+    if field is not None:
+        fc = _f64(field).reshape(int(n_steps))
+        fp = fc.ctypes.data
+    h = float(spacing[0]) if np.ndim(spacing) else float(spacing)
+    rc = _load().orc_dirac1d_propagate(y.ctypes.data, Vp, n, h, mass, charge, hbar, c, float(dt),
+                                       int(n_steps), fp)
+    if rc != 0:
+        raise ValueError("unsupported shape")
+    return y
+
+
+def dirac1d_u(p: float, mass: float = 1.0, c: float = 137.036) -> np.ndarray:
+    """The 2x2 u(p) of the 1D Dirac split (Eq. 30's form)."""
+    out = np.empty(4, dtype=np.complex128)
+    _load().orc_dirac1d_u(float(p), mass, c, out.ctypes.data)
+    return out.reshape(2, 2)
+
+
+def dirac1d_h(p: float, mass: float = 1.0, c: float = 137.036) -> np.ndarray:
+    """c alpha_1 p + m c^2 beta with alpha_1 = sigma_x, beta = sigma_z."""
+    out = np.empty(4, dtype=np.complex128)
+    _load().orc_dirac1d_h(float(p), mass, c, out.ctypes.data)
+    return out.reshape(2, 2)
+
+
 def alpha_beta():
     """alpha_1..3 and beta of the Dirac representation (Eq. 16)."""
     out = np.empty(64, dtype=np.complex128)
@@ -291,7 +338,8 @@ def norm(psi, spacing, comps: int = 1) -> float:
 def energy(psi, V, spacing, comps: int = 1, mass: float = 1.0, hbar: float = 1.0,
            c: float = 137.036) -> float:
     """Field-free energy <T> + <V>; T = p^2/2m (comps=1) or the free Dirac
-    Hamiltonian of Eq. 28 (comps=4)."""
+    Hamiltonian of Eq. 28 (comps=4 in 2D/3D, comps=2 in 1D with
+    alpha_1 = sigma_x, beta = sigma_z)."""
     y = _c128(psi)
     sp = y.shape[1:] if comps > 1 else y.shape
     Vp = None

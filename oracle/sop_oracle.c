@@ -510,6 +510,113 @@ int orc_dirac_propagate(cplx *psi, const double *V, int ndim, const int64_t *dim
 }
 
 /* ------------------------------------------------------------------ */
+/* One-dimensional Dirac equation, two components (end of Sec. 2.3)    */
+/* ------------------------------------------------------------------ */
+
+/* The paper writes the 1D operators with alpha_1 and beta without printing
+ * their 2x2 form; this oracle takes alpha_1 = sigma_x, beta = sigma_z (they
+ * anticommute and square to one, as Eq. 15 requires). */
+static void dirac1d_matrices(cplx al[2][2], cplx be[2][2]) {
+    al[0][0] = 0; al[0][1] = 1; al[1][0] = 1; al[1][1] = 0;
+    be[0][0] = 1; be[0][1] = 0; be[1][0] = 0; be[1][1] = -1;
+}
+
+/* u(p) = d_+ + d_- (p/|p|) beta alpha_1 with d_+- of Eq. 29: the 2x2 form of
+ * Eq. 30, which turns c alpha_1 p + m c^2 beta into diag(E, -E). */
+static void dirac1d_u(double p, double mass, double c, cplx u[2][2]) {
+    cplx al[2][2], be[2][2];
+    dirac1d_matrices(al, be);
+    const double root = sqrt(1.0 + p * p / ((mass * c) * (mass * c)));
+    const double dp = sqrt(0.5 + 0.5 / root);
+    const double dm = sqrt(0.5 - 0.5 / root);
+    const double sgn = p > 0.0 ? 1.0 : (p < 0.0 ? -1.0 : 0.0);
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            cplx ba = 0;
+            for (int k = 0; k < 2; ++k) ba += be[i][k] * al[k][j];
+            u[i][j] = (i == j ? dp : 0.0) + dm * sgn * ba;
+        }
+}
+
+void orc_dirac1d_u(double p, double mass, double c, double *out /* 4 complex */) {
+    cplx u[2][2];
+    dirac1d_u(p, mass, c, u);
+    memcpy(out, u, sizeof(cplx) * 4);
+}
+
+/* H = c alpha_1 p + m c^2 beta (Eq. 28 in one dimension). */
+static void dirac1d_h(double p, double mass, double c, cplx H[2][2]) {
+    cplx al[2][2], be[2][2];
+    dirac1d_matrices(al, be);
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) H[i][j] = c * p * al[i][j] + mass * c * c * be[i][j];
+}
+
+void orc_dirac1d_h(double p, double mass, double c, double *out) {
+    cplx H[2][2];
+    dirac1d_h(p, mass, c, H);
+    memcpy(out, H, sizeof(cplx) * 4);
+}
+
+/* Momentum-space factor of the 1D Dirac equation:
+ *   v <- u^dagger diag(e^{-iE tau/hbar}, e^{iE tau/hbar}) u v,  E = sqrt(m^2 c^4 + p^2 c^2). */
+static void dirac1d_kinetic_apply(double p, double mass, double c, double hbar, double tau, cplx v[2]) {
+    cplx u[2][2];
+    dirac1d_u(p, mass, c, u);
+    const double E = sqrt(mass * mass * c * c * c * c + p * p * c * c);
+    const double ang = E * tau / hbar;
+    cplx w[2];
+    for (int i = 0; i < 2; ++i) w[i] = u[i][0] * v[0] + u[i][1] * v[1];
+    w[0] *= cos(ang) - I * sin(ang);
+    w[1] *= cos(ang) + I * sin(ang);
+    for (int i = 0; i < 2; ++i) v[i] = conj(u[0][i]) * w[0] + conj(u[1][i]) * w[1];
+}
+
+/* Real-space half factor: exp(-i tau V/(2 hbar)) times the 1D mixing
+ * R = cos(theta) + i alpha_1 sin(theta), theta = delta q c Abar / hbar,
+ * Abar = A tau (midpoint rule); for q = -1 this is the printed form. */
+static void dirac1d_real_space(cplx *psi, const double *V, int64_t n, const double *A, double charge,
+                               double c, double hbar, double tau) {
+    cplx al[2][2], be[2][2];
+    dirac1d_matrices(al, be);
+    const double theta = 0.5 * charge * c * (A ? *A * tau : 0.0) / hbar;
+    cplx R[2][2];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) R[i][j] = (i == j ? cos(theta) : 0.0) + I * sin(theta) * al[i][j];
+    for (int64_t j = 0; j < n; ++j) {
+        const cplx a = psi[j], b = psi[n + j];
+        const double ang = -0.5 * tau * (V ? V[j] : 0.0) / hbar;
+        const cplx ph = cos(ang) + I * sin(ang);
+        psi[j] = ph * (R[0][0] * a + R[0][1] * b);
+        psi[n + j] = ph * (R[1][0] * a + R[1][1] * b);
+    }
+}
+
+/* n_steps Strang steps (Eq. 8) of the two-component 1D Dirac equation:
+ * psi is [2][n]; field: n_steps vector-potential samples A_1 (midpoints) or NULL. */
+int orc_dirac1d_propagate(cplx *psi, const double *V, int64_t n, double h, double mass, double charge,
+                          double hbar, double c, double tau, int64_t n_steps, const double *field) {
+    if (!orc_size_ok(n)) return -1;
+    const int64_t dims[1] = {n};
+    for (int64_t s = 0; s < n_steps; ++s) {
+        const double *A = field ? field + s : NULL;
+        dirac1d_real_space(psi, V, n, A, charge, c, hbar, tau);
+        orc_fftn(psi, 1, dims, -1);
+        orc_fftn(psi + n, 1, dims, -1);
+        for (int64_t k = 0; k < n; ++k) {
+            cplx v[2] = {psi[k], psi[n + k]};
+            dirac1d_kinetic_apply(lattice_p(n, h, k, hbar), mass, c, hbar, tau, v);
+            psi[k] = v[0];
+            psi[n + k] = v[1];
+        }
+        orc_fftn(psi, 1, dims, +1);
+        orc_fftn(psi + n, 1, dims, +1);
+        dirac1d_real_space(psi, V, n, A, charge, c, hbar, tau);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Reductions                                                          */
 /* ------------------------------------------------------------------ */
 
@@ -573,6 +680,13 @@ double orc_energy(const cplx *psi, const double *V, int ndim, const int64_t *dim
         if (comps == 1) {
             cplx z = pt[k];
             kahan_add(&kt, (p2 / (2.0 * mass)) * (creal(z) * creal(z) + cimag(z) * cimag(z)));
+        } else if (comps == 2) {
+            cplx H[2][2];
+            dirac1d_h(p[0], mass, c, H);
+            cplx s = 0;
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j) s += conj(pt[i * N + k]) * H[i][j] * pt[j * N + k];
+            kahan_add(&kt, creal(s));
         } else {
             cplx H[4][4];
             dirac_h(p, ndim, mass, c, H);

@@ -6,10 +6,13 @@
 // lambda_m = U_m^dagger lambda_{m+1}) the gradient needs, for every m,
 //   <lambda_m|psi_m>, <lambda_m|X_a|psi_m>   (inner products, k_inner)
 //   acc_j += w_m conj(lambda_{m,j}) psi_{m,j}  (per point, k_accum)
-// and finally dJ/dV_j = 2 Re(conj(c) k_V dV acc_j) (k_grad_v).
+// and finally dJ/dV_j = 2 Re(conj(c) k_V dV acc_j) (k_grad_v).  The same
+// file holds the reductions of the spectral method (k_spectral_*).
 //
-// Reductions use a fixed grid and a fixed-order final sum in FP64, like
-// sop_reduce.cu, so results are deterministic run to run.
+// Reductions use a fixed grid and a fixed-order final sum, so results are
+// deterministic run to run.  Per-point work avoids FP64 instructions (GB300
+// runs about one FP64 operation per SM per clock): sums stay in the state's
+// precision, as float pairs (two-sum) for complex64, and reach FP64 per warp.
 #include <type_traits>
 
 #include "sop_fft.cuh"
@@ -29,115 +32,6 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
-
-struct InnerGeom {
-    int ndim;
-    int64_t dims[3];
-    double x0[3], h[3];   // x_{a,i} = x0[a] + i h[a]
-};
-
-// Products and coordinates are formed in the precision of the state (FP32
-// for complex64); each thread sums kChunk points in that precision and adds
-// the chunk sums in FP64 (FP64 arithmetic is a small fraction of the FP32
-// rate on GB300, and a 16-term FP32 sum errs by ~1e-6 relative).
-constexpr int kChunk = 16;
-
-template <typename C>
-__global__ void __launch_bounds__(kThreads) k_inner(const C *a, const C *b, int64_t npts, InnerGeom g, double *partial) {
-    using R = decltype(C{}.x);
-    double acc[kVals];
-#pragma unroll
-    for (int k = 0; k < kVals; ++k) acc[k] = 0.0;
-    R x0[3], hh[3];
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-        x0[ax] = (R)g.x0[ax];
-        hh[ax] = (R)g.h[ax];
-    }
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
-    int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    while (j < npts) {
-        R loc[kVals];
-#pragma unroll
-        for (int k = 0; k < kVals; ++k) loc[k] = R(0);
-        for (int q = 0; q < kChunk && j < npts; ++q, j += stride) {
-            const C u = a[j], v = b[j];
-            const R re = u.x * v.x + u.y * v.y;   // conj(u) v
-            const R im = u.x * v.y - u.y * v.x;
-            loc[0] += re;
-            loc[1] += im;
-            // lattice index per axis, in 32 bits (sop_adjoint_gradient accepts
-            // lattices of fewer than 2^31 points)
-            uint32_t r = (uint32_t)j;
-#pragma unroll
-            for (int ax = 0; ax < 3; ++ax) {
-                if (ax < g.ndim) {
-                    const uint32_t n = (uint32_t)g.dims[ax];
-                    const uint32_t i = r % n;
-                    r /= n;
-                    const R x = x0[ax] + (R)i * hh[ax];
-                    loc[2 + 2 * ax] += x * re;
-                    loc[3 + 2 * ax] += x * im;
-                }
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < kVals; ++k) acc[k] += (double)loc[k];
-    }
-    __shared__ double ws[kVals][kThreads / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < kVals; ++k) {
-        const double sum = warp_sum(acc[k]);
-        if (lane == 0) ws[k][wid] = sum;
-    }
-    __syncthreads();
-    if (threadIdx.x < kVals) {
-        double sum = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) sum += ws[threadIdx.x][w];
-        partial[(int64_t)blockIdx.x * kVals + threadIdx.x] = sum;
-    }
-}
-
-// out[k] = scale * sum over blocks: warp k sums value k (fixed order).
-__global__ void k_inner_final(const double *partial, int nb, double scale, double *out) {
-    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (k < kVals) {
-        double sum = 0.0;
-        for (int i = lane; i < nb; i += 32) sum += partial[(int64_t)i * kVals + k];
-        sum = warp_sum(sum);
-        if (lane == 0) out[k] = scale * sum;
-    }
-}
-
-// acc_j += w conj(a_j) b_j: the product in the state's precision, the sum in FP64.
-template <typename C>
-__global__ void __launch_bounds__(kThreads) k_accum(const C *a, const C *b, int64_t npts, double w, double2 *acc) {
-    using R = decltype(C{}.x);
-    const R wr = (R)w;
-    for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < npts; j += (int64_t)gridDim.x * kThreads) {
-        const C u = a[j], v = b[j];
-        double2 s = acc[j];
-        s.x += (double)(wr * (u.x * v.x + u.y * v.y));
-        s.y += (double)(wr * (u.x * v.y - u.y * v.x));
-        acc[j] = s;
-    }
-}
-
-// Spectral method.  Per time sample, k_spectral_sample forms the partial
-// sums of conj(psi0_j) psi_j (products in the state's precision, summed over
-// kUnroll points per thread in that precision, then as a float pair per
-// thread and warp, then in FP64 per block) and, for the
-// eigenfunctions, copies psi_n into one slot of a ring of up to kRing states;
-// every kRing samples k_spectral_accum adds sum_b w_{b,k} psi_b,j into the
-// FP64 accumulator of each energy k, so that the accumulators are read and
-// written once per kRing steps instead of every step.  Loads of kUnroll
-// points are issued before any is used (the memory-level parallelism a
-// bandwidth-bound reduction needs with 16 warps per SM).
-constexpr int kUnroll = 4;
-constexpr int kSampleBlocks = kBlocks * 4;
-static_assert(2 * kSampleBlocks <= kBlocks * kVals, "sample partials fit the inner-product partial buffer");
-constexpr int kRing = SOP_SPECTRAL_RING;
 
 // s + e = a + b exactly (Knuth's two-sum; explicit round-to-nearest adds so
 // that nothing is contracted or reassociated).
@@ -175,6 +69,129 @@ template <typename R> struct PairSum {
     }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
+
+struct InnerGeom {
+    int ndim;
+    int64_t dims[3];
+    double x0[3], h[3];   // x_{a,i} = x0[a] + i h[a]
+};
+
+// Products and coordinates are formed in the precision of the state (FP32
+// for complex64); each thread sums kChunk points in that precision, keeps
+// the chunk sums as float pairs (PairSum: no FP64 instruction per point, the
+// FP64 pipe being a small fraction of FP32 on this part), reduces them over
+// the warp as pairs and only then adds in FP64 (per warp and block).
+constexpr int kChunk = 16;
+
+template <typename C>
+__global__ void __launch_bounds__(kThreads) k_inner(const C *a, const C *b, int64_t npts, InnerGeom g, double *partial) {
+    using R = decltype(C{}.x);
+    PairSum<R> acc[kVals];
+    R x0[3], hh[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        x0[ax] = (R)g.x0[ax];
+        hh[ax] = (R)g.h[ax];
+    }
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    while (j < npts) {
+        R loc[kVals];
+#pragma unroll
+        for (int k = 0; k < kVals; ++k) loc[k] = R(0);
+        for (int q = 0; q < kChunk && j < npts; ++q, j += stride) {
+            const C u = a[j], v = b[j];
+            const R re = u.x * v.x + u.y * v.y;   // conj(u) v
+            const R im = u.x * v.y - u.y * v.x;
+            loc[0] += re;
+            loc[1] += im;
+            // lattice index per axis, in 32 bits (sop_adjoint_gradient accepts
+            // lattices of fewer than 2^31 points)
+            uint32_t r = (uint32_t)j;
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                if (ax < g.ndim) {
+                    const uint32_t n = (uint32_t)g.dims[ax];
+                    const uint32_t i = r % n;
+                    r /= n;
+                    const R x = x0[ax] + (R)i * hh[ax];
+                    loc[2 + 2 * ax] += x * re;
+                    loc[3 + 2 * ax] += x * im;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kVals; ++k) acc[k].add(loc[k]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < kVals; ++k) acc[k].add(acc[k].shfl_xor(o));
+    __shared__ double ws[kVals][kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < kVals; ++k) ws[k][wid] = acc[k].value();
+    __syncthreads();
+    if (threadIdx.x < kVals) {
+        double sum = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) sum += ws[threadIdx.x][w];
+        partial[(int64_t)blockIdx.x * kVals + threadIdx.x] = sum;
+    }
+}
+
+// out[k] = scale * sum over blocks: warp k sums value k (fixed order).
+__global__ void k_inner_final(const double *partial, int nb, double scale, double *out) {
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (k < kVals) {
+        double sum = 0.0;
+        for (int i = lane; i < nb; i += 32) sum += partial[(int64_t)i * kVals + k];
+        sum = warp_sum(sum);
+        if (lane == 0) out[k] = scale * sum;
+    }
+}
+
+// acc_j += w conj(a_j) b_j, the product in the state's precision.  Complex128:
+// FP64 accumulators; complex64: float pairs (hi.re, hi.im, lo.re, lo.im) in
+// the same 16 bytes, updated by two-sum (read back by k_grad_v).
+template <typename C>
+__global__ void __launch_bounds__(kThreads) k_accum(const C *a, const C *b, int64_t npts, double w, double2 *acc) {
+    using R = decltype(C{}.x);
+    constexpr bool kPair = sizeof(R) == 4;
+    using A = typename std::conditional<kPair, float4, double2>::type;
+    A *ac = reinterpret_cast<A *>(acc);
+    const R wr = (R)w;
+    for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < npts; j += (int64_t)gridDim.x * kThreads) {
+        const C u = a[j], v = b[j];
+        A s = ac[j];
+        const R px = wr * (u.x * v.x + u.y * v.y), py = wr * (u.x * v.y - u.y * v.x);
+        if constexpr (kPair) {
+            float hx, ex, hy, ey;
+            two_sum(s.x, px, hx, ex);
+            two_sum(s.y, py, hy, ey);
+            s = make_float4(hx, hy, s.z + ex, s.w + ey);
+        } else {
+            s.x += px;
+            s.y += py;
+        }
+        ac[j] = s;
+    }
+}
+
+// Spectral method.  Per time sample, k_spectral_sample forms the partial
+// sums of conj(psi0_j) psi_j (products in the state's precision, summed over
+// kUnroll points per thread in that precision, then as a float pair per
+// thread and warp, then in FP64 per block) and, for the
+// eigenfunctions, copies psi_n into one slot of a ring of up to kRing states;
+// every kRing samples k_spectral_accum adds sum_b w_{b,k} psi_b,j into the
+// FP64 accumulator of each energy k, so that the accumulators are read and
+// written once per kRing steps instead of every step.  Loads of kUnroll
+// points are issued before any is used (the memory-level parallelism a
+// bandwidth-bound reduction needs with 16 warps per SM).
+constexpr int kUnroll = 4;
+constexpr int kSampleBlocks = kBlocks * 4;
+static_assert(2 * kSampleBlocks <= kBlocks * kVals, "sample partials fit the inner-product partial buffer");
+constexpr int kRing = SOP_SPECTRAL_RING;
 
 template <typename C>
 __global__ void __launch_bounds__(kThreads) k_spectral_sample(const C *__restrict__ psi0, const C *__restrict__ psi,
@@ -354,11 +371,21 @@ __global__ void __launch_bounds__(kThreads) k_spectrum(const double *chi, int64_
     }
 }
 
-// g_j = 2 Re(z acc_j) with z = conj(c) k_V dV given as (zr, zi).
+// g_j = 2 Re(z acc_j) with z = conj(c) k_V dV given as (zr, zi); acc as
+// k_accum left it (float pairs for complex64 states).
+template <bool kPair>
 __global__ void __launch_bounds__(kThreads) k_grad_v(const double2 *acc, int64_t npts, double zr, double zi, double *g) {
     for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < npts; j += (int64_t)gridDim.x * kThreads) {
-        const double2 s = acc[j];
-        g[j] = 2.0 * (zr * s.x - zi * s.y);
+        double sx, sy;
+        if constexpr (kPair) {
+            const float4 f = reinterpret_cast<const float4 *>(acc)[j];
+            sx = (double)f.x + (double)f.z;
+            sy = (double)f.y + (double)f.w;
+        } else {
+            sx = acc[j].x;
+            sy = acc[j].y;
+        }
+        g[j] = 2.0 * (zr * sx - zi * sy);
     }
 }
 
@@ -447,8 +474,13 @@ cudaError_t launch_spectrum(const double *chi, int64_t N, double dt, double hbar
     return cudaGetLastError();
 }
 
-cudaError_t launch_grad_v(const double *acc, int64_t npts, double zr, double zi, double *g, cudaStream_t s) {
-    k_grad_v<<<kBlocks * 4, kThreads, 0, s>>>(reinterpret_cast<const double2 *>(acc), npts, zr, zi, g);
+cudaError_t launch_grad_v(const double *acc, bool f64, int64_t npts, double zr, double zi, double *g,
+                          cudaStream_t s) {
+    const double2 *ac = reinterpret_cast<const double2 *>(acc);
+    if (f64)
+        k_grad_v<false><<<kBlocks * 4, kThreads, 0, s>>>(ac, npts, zr, zi, g);
+    else
+        k_grad_v<true><<<kBlocks * 4, kThreads, 0, s>>>(ac, npts, zr, zi, g);
     return cudaGetLastError();
 }
 

@@ -1415,7 +1415,7 @@ int sop_adjoint_gradient(sop_plan p, const void *phi_dev, int64_t n_steps, doubl
             }
     if (grad_V_dev) {
         const cd z = std::conj(c) * kV * dV;
-        e = launch_grad_v(acc, p->npts, z.real(), z.imag(), grad_V_dev, p->stream);
+        e = launch_grad_v(acc, p->f64, p->npts, z.real(), z.imag(), grad_V_dev, p->stream);
         p->launches += 1;
         if (e != cudaSuccess) {
             cleanup();

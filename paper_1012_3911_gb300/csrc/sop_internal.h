@@ -128,7 +128,9 @@ cudaError_t launch_async_f64_strided(const PassArgs &a, int nc, const TensorMapB
 int inner_partials();
 cudaError_t launch_inner(const void *a, const void *b, bool f64, int ndim, const int64_t *dims, const double *h,
                          double dV, double *partial, double *out, cudaStream_t s);
-// acc[2j], acc[2j+1] += w conj(a_j) b_j
+// acc_j += w conj(a_j) b_j, 16 bytes per point: complex128 (f64) or, for
+// complex64 states, the float pair (hi.re, hi.im, lo.re, lo.im) that
+// launch_grad_v reads back
 cudaError_t launch_accum(const void *a, const void *b, bool f64, int64_t npts, double w, double *acc,
                          cudaStream_t s);
 // Spectral method.  launch_spectral_sample: chi[0..1] = dV <psi0|psi> and,
@@ -150,8 +152,9 @@ cudaError_t launch_spectral_accum(const void *ring, bool f64, int B, int64_t len
 cudaError_t launch_spectral_finish(double *acc, bool f64, int64_t n, cudaStream_t s);
 cudaError_t launch_spectrum(const double *chi, int64_t N, double dt, double hbar, const double *E, int K,
                             double *spec, cudaStream_t s);
-// g_j = 2 Re((zr + i zi) (acc[2j] + i acc[2j+1]))
-cudaError_t launch_grad_v(const double *acc, int64_t npts, double zr, double zi, double *g, cudaStream_t s);
+// g_j = 2 Re((zr + i zi) acc_j), acc as launch_accum left it
+cudaError_t launch_grad_v(const double *acc, bool f64, int64_t npts, double zr, double zi, double *g,
+                          cudaStream_t s);
 
 // Per-stage twiddle table of an n-point axis for the persistent passes:
 // out == nullptr returns its entry count, else fills out from tw (async);

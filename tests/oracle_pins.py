@@ -457,6 +457,108 @@ def pin_dirac_uniform_A_second_order(orc):
     assert 3.5 < errs[0] / errs[1] < 4.5, errs
 
 
+SX = np.array([[0, 1], [1, 0]], dtype=complex)
+SZ = np.array([[1, 0], [0, -1]], dtype=complex)
+
+
+def _h1(p, m=1.0, c=C):
+    """1D Dirac Hamiltonian c sigma_x p + m c^2 sigma_z, written here."""
+    return c * p * SX + m * c * c * SZ
+
+
+def pin_dirac1d_u_diagonalises(orc):
+    """The 2x2 u(p) is unitary and u H u^dag = diag(E, -E) (the 1D form of
+    Eqs. 29-32), including p = 0, both signs and |p| >> mc."""
+    for p in (0.0, 0.7, -3.1, 250.0, -1.0e4):
+        u = orc.dirac1d_u(p)
+        H = orc.dirac1d_h(p)
+        assert np.abs(H - _h1(p)).max() < 1e-9 * max(1.0, abs(p) * C)
+        E = np.sqrt(C ** 4 + p * p * C * C)
+        assert np.abs(u @ u.conj().T - np.eye(2)).max() < 1e-14
+        assert np.abs(u @ _h1(p) @ u.conj().T - np.diag([E, -E])).max() < 1e-10 * E
+
+
+def pin_dirac1d_free_exact(orc):
+    """V = 0, A = 0: per momentum psi~(t) = expm(-i H(p) t) psi~(0) (scipy),
+    for a random two-component spinor including the Nyquist index."""
+    n, h = 24, 0.02
+    psi0 = wl.random_state((2, n), 91)
+    tau, steps = 3e-4, 6
+    out = orc.dirac1d_propagate(psi0, None, (h,), tau, steps)
+    st = np.fft.fft(psi0, axis=1)
+    for k, p in enumerate(wl.momenta(n, h)):
+        st[:, k] = scipy.linalg.expm(-1j * tau * steps * _h1(p)) @ st[:, k]
+    assert relerr(out, np.fft.ifft(st, axis=1)) < 1e-12
+
+
+def pin_dirac1d_constant_potential_phase(orc):
+    n, h = 32, 0.05
+    psi0 = wl.random_state((2, n), 92)
+    V0, tau, steps = 321.5, 2e-4, 5
+    out = orc.dirac1d_propagate(psi0, np.full(n, V0), (h,), tau, steps)
+    ref = np.exp(-1j * V0 * tau * steps) * orc.dirac1d_propagate(psi0, None, (h,), tau, steps)
+    assert relerr(out, ref) < 1e-12
+
+
+def pin_dirac1d_norm_and_reversibility(orc):
+    n, h = 48, 0.04
+    psi0 = wl.random_state((2, n), 93, (h,))
+    V = wl.random_potential((n,), 94, 5.0)
+    A = wl.random_field(7, 1, 95, 40.0)[:, 0]
+    out = orc.dirac1d_propagate(psi0, V, (h,), 1e-4, 7, A)
+    assert abs(orc.norm(out, (h,), 2) - orc.norm(psi0, (h,), 2)) < 1e-12
+    back = orc.dirac1d_propagate(out, V, (h,), -1e-4, 7, A[::-1].copy())
+    assert relerr(back, psi0) < 1e-12
+
+
+def pin_dirac1d_equals_2d_pair(orc):
+    """The two-component 1D equation is the (1,4) component pair of the
+    four-component 2D code on a state constant along y (p_y = 0), with the
+    same V(x) and A = (A_x, 0): two independent oracle paths (4x4 u(p) of
+    Eq. 30 and the mixing of Eq. 26 against their 2x2 forms)."""
+    nx, ny, h = 32, 8, (0.05, 0.1)
+    psi1 = wl.random_state((2, nx), 96, (h[0],))
+    V = wl.random_potential((nx,), 97, 20.0)
+    A = wl.random_field(5, 1, 98, 60.0)[:, 0]
+    tau = 2e-4
+    one = orc.dirac1d_propagate(psi1, V, (h[0],), tau, 5, A)
+    psi2 = np.zeros((4, ny, nx), dtype=complex)
+    psi2[0] = psi1[0][None, :]
+    psi2[3] = psi1[1][None, :]
+    F = np.stack([A, np.zeros_like(A)], axis=1)
+    two = orc.dirac_propagate(psi2, np.tile(V, (ny, 1)), h, tau, 5, F)
+    assert np.abs(two[1]).max() < 1e-13 and np.abs(two[2]).max() < 1e-13
+    assert relerr(two[0][0], one[0]) < 1e-12 and relerr(two[3][3], one[1]) < 1e-12
+
+
+def pin_dirac1d_uniform_A_second_order(orc):
+    """Constant A, V = 0: exact evolution expm(-i H(p - qA) t) per momentum
+    (q = -1); the split converges at second order."""
+    c = 10.0
+    n, h = 32, 0.3
+    psi0 = wl.random_smooth_state((n,), (h,), 99, comps=2)
+    A, t = 0.8, 0.2
+    st = np.fft.fft(psi0, axis=1)
+    for k, p in enumerate(wl.momenta(n, h)):
+        st[:, k] = scipy.linalg.expm(-1j * t * _h1(p + A, 1.0, c)) @ st[:, k]
+    ref = np.fft.ifft(st, axis=1)
+    errs = [relerr(orc.dirac1d_propagate(psi0, None, (h,), t / m, m, np.full(m, A), c=c), ref) for m in (20, 40)]
+    assert errs[0] < 5e-2, errs
+    assert 3.5 < errs[0] / errs[1] < 4.5, errs
+
+
+def pin_dirac1d_energy(orc):
+    """<H> of a 1D spinor: (dV/N) sum_k psi~^dag H(p) psi~ + dV sum V |psi|^2,
+    written here with NumPy's FFT."""
+    n, h = 64, 0.05
+    psi = wl.random_state((2, n), 100, (h,))
+    V = wl.random_potential((n,), 101, 3.0)
+    st = np.fft.fft(psi, axis=1)
+    t = sum(np.vdot(st[:, k], _h1(p) @ st[:, k]).real for k, p in enumerate(wl.momenta(n, h)))
+    ref = h / n * t + h * np.sum(V * np.sum(np.abs(psi) ** 2, axis=0))
+    assert abs(orc.energy(psi, V, (h,), 2) - ref) < 1e-10 * abs(ref)
+
+
 def pin_dirac_velocity(orc):
     """Sec. 5.1: a positive-energy packet with mean momentum (40, 0) moves
     at |p|/(m sqrt(1 + p^2/(mc)^2)) = 38.398 a.u."""
@@ -497,7 +599,9 @@ ALL_PINS = [
     pin_free_schrodinger_exact, pin_free_gaussian_spreading, pin_coherent_state_second_order,
     pin_coherent_state_period, pin_schrodinger_norm_and_reversibility, pin_constant_potential_phase,
     pin_shift_covariance, pin_field_kick_plane_wave, pin_velocity_gauge_plane_waves,
-    pin_velocity_gauge_lattice_shift, pin_ehrenfest_field, pin_schrodinger_energy,
+    pin_velocity_gauge_lattice_shift, pin_dirac1d_u_diagonalises, pin_dirac1d_free_exact,
+    pin_dirac1d_constant_potential_phase, pin_dirac1d_norm_and_reversibility, pin_dirac1d_equals_2d_pair,
+    pin_dirac1d_uniform_A_second_order, pin_dirac1d_energy, pin_ehrenfest_field, pin_schrodinger_energy,
     pin_dirac_algebra, pin_dirac_u_diagonalises, pin_dirac_kinetic_expm, pin_dirac_mixing_expm,
     pin_free_dirac_exact, pin_dirac_constant_potential_phase, pin_dirac_norm_and_reversibility, pin_dirac_uniform_A_second_order,
     pin_dirac_velocity, pin_dirac_energy,

@@ -37,6 +37,16 @@ MUTANTS = [
      [pins.pin_velocity_gauge_plane_waves, pins.pin_velocity_gauge_lattice_shift]),
     ("velocity_gauge_drops_A", "if (A) p -= charge * A[a];", "(void)A;",
      [pins.pin_velocity_gauge_plane_waves, pins.pin_velocity_gauge_lattice_shift]),
+    ("dirac1d_u_sign", "u[i][j] = (i == j ? dp : 0.0) + dm * sgn * ba;",
+     "u[i][j] = (i == j ? dp : 0.0) - dm * sgn * ba;",
+     [pins.pin_dirac1d_u_diagonalises, pins.pin_dirac1d_free_exact]),
+    ("dirac1d_mixing_sign", "R[i][j] = (i == j ? cos(theta) : 0.0) + I * sin(theta) * al[i][j];",
+     "R[i][j] = (i == j ? cos(theta) : 0.0) - I * sin(theta) * al[i][j];",
+     [pins.pin_dirac1d_equals_2d_pair, pins.pin_dirac1d_uniform_A_second_order]),
+    ("dirac1d_beta_sign", "be[1][0] = 0; be[1][1] = -1;", "be[1][0] = 0; be[1][1] = 1;",
+     [pins.pin_dirac1d_u_diagonalises, pins.pin_dirac1d_free_exact]),
+    ("dirac1d_energy_u_not_h", "dirac1d_h(p[0], mass, c, H);", "dirac1d_u(p[0], mass, c, H);",
+     [pins.pin_dirac1d_energy]),
     ("lattice_origin", "return -0.5 * (double)n * h + (double)j * h;",
      "return -0.5 * (double)n * h + (double)(j + 1) * h;", [pins.pin_field_kick_plane_wave]),
     ("dirac_u_not_adjoint", "for (int k = 0; k < 4; ++k) s += conj(u[k][i]) * w[k];",
