@@ -278,6 +278,7 @@ def main():
     adjoint = None
     spectral = None
     velocity = None
+    dirac1d = None
     if args.batched and rank == 0:
         ws = wl.config5(64, n_steps=args.batch_steps)
         npts5 = sum(x.npoints for x in ws)
@@ -389,6 +390,30 @@ def main():
                     "ratio_to_length_gauge": tv / (total_ms * 1e-3 / args.steps)}
         qv.close()
         torch.cuda.empty_cache()
+        # one-dimensional two-component Dirac equation (whole steps on chip):
+        # 4096 points on [-4, 4), soft core Z = 1, a^2 = 0.01, A_1 = 20 sin^2 cos 2t
+        n1, T1 = 4096, 2000
+        h1 = 8.0 / n1
+        x1 = wl.lattice(n1, h1)
+        t1 = (np.arange(T1) + 0.5) * 1e-4
+        A1 = (20.0 * np.sin(np.pi * t1 / (T1 * 1e-4)) ** 2 * np.cos(2.0 * t1)).reshape(T1, 1)
+        psi1 = wl.dirac_positive_spin_up(wl.gaussian((n1, 1), (h1, 1.0), (0.0, 0.0), 0.5, (50.0, 0.0)),
+                                         (n1, 1), (h1, 1.0))[[0, 3], 0, :]
+        qd = sop.Propagator((n1,), (h1,), 2, "c64")
+        qd.set_potential(-1.0 / np.sqrt(x1 * x1 + 0.01))
+        qd.set_state(torch.from_numpy(psi1))
+        qd.step(20, 1e-4, A1[:20])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        qd.step(T1, 1e-4, A1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        td = e0.elapsed_time(e1) * 1e-3
+        dirac1d = {"value": n1 * T1 / td, "unit": UNIT, "dtype": "f32",
+                   "workload": f"1D two-component Dirac, {n1} points on [-4,4), soft core Z=1 (a^2 0.01), "
+                               f"A_1 = 20 sin^2 cos 2t, dt 1e-4, {T1} steps, one CTA keeps the line on chip",
+                   "us_per_step": td / T1 * 1e6}
+        qd.close()
 
     # ---- FP64 sample, same lattice -----------------------------------------
     fp64 = None
@@ -483,7 +508,7 @@ def main():
                              "within a step",
                        "parallelism": f"replicas x{world} (independent problems, no data-path collective)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "fp64": fp64, "batched": batched, "adjoint": adjoint, "spectral": spectral, "velocity_gauge": velocity, "err_vs_oracle": err, "clocks": clocks,
+            "fp64": fp64, "batched": batched, "adjoint": adjoint, "spectral": spectral, "velocity_gauge": velocity, "dirac1d": dirac1d, "err_vs_oracle": err, "clocks": clocks,
         }
         s = json.dumps(line)
         print(s, flush=True)

@@ -1,5 +1,5 @@
-// sop_1d_inst.cu -- instantiates the one-dimensional whole-step kernel for
-// one dtype (-DSOP_REAL=float|double, with -DSOP_IS_DOUBLE=1 for double); the
+// sop_1d_inst.cu -- instantiates the one-dimensional whole-step kernels
+// (Schroedinger and two-component Dirac) for one dtype (-DSOP_REAL=float|double, with -DSOP_IS_DOUBLE=1 for double); the
 // double build also defines the pass-geometry query and the shared-memory
 // attribute helper.
 #include <map>
@@ -28,6 +28,22 @@ cudaError_t launch_1d_f32(const Args1D &a, int n, cudaStream_t s) {
 #define SOP_CASE(N) \
     case N:         \
         return launch_1d_t<SOP_REAL, N>(a, s);
+        SOP_SIZES(SOP_CASE)
+#undef SOP_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+#if SOP_IS_DOUBLE
+cudaError_t launch_1d_dirac_f64(const Args1D &a, int n, cudaStream_t s) {
+#else
+cudaError_t launch_1d_dirac_f32(const Args1D &a, int n, cudaStream_t s) {
+#endif
+    switch (n) {
+#define SOP_CASE(N) \
+    case N:         \
+        return launch_1d_dirac_t<SOP_REAL, N>(a, s);
         SOP_SIZES(SOP_CASE)
 #undef SOP_CASE
         default:

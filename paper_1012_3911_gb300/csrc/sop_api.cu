@@ -79,6 +79,8 @@ struct sop_plan_s {
     void *vhalf = nullptr, *vfull = nullptr;
     void *kin[3] = {nullptr, nullptr, nullptr};
     void *dtab = nullptr;
+    void *mtab = nullptr;           // 1D Dirac: merged mixing rows of one call
+    size_t mtab_cap = 0;
     double *theta = nullptr;        // device scratch for per-axis angles
     double tables_dt = std::nan("");
     bool tables_valid = false;
@@ -229,6 +231,7 @@ int plan_free(sop_plan p) {
     dfree(p->vhalf);
     dfree(p->vfull);
     dfree(p->dtab);
+    dfree(p->mtab);
     dfree(p->theta);
     dfree(p->ftab);
     dfree(p->fvec);
@@ -558,6 +561,69 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
         return (field && s >= 0 && s < n) ? field[s * nd + a] : 0.0;
     };
 
+    if (p->comps == 2) {
+        // ---- Dirac, 1D, two components: whole steps on chip ----------------
+        // merged mixing M_P = R(A_P) R(A_{P-1}), R(A) = cos th + i sin th sigma_x,
+        // th = q c A tau / (2 hbar) (the half-step factor; A = 0 beyond the call)
+        auto R = [&](int64_t s, cd M[2][2]) {
+            const double th = (field && s >= 0 && s < n) ? 0.5 * p->prm.charge * p->prm.c * field[s] * dt / hbar : 0.0;
+            M[0][0] = M[1][1] = std::cos(th);
+            M[0][1] = M[1][0] = cd(0.0, std::sin(th));
+        };
+        const size_t row_bytes = 4 * p->csz;
+        const size_t bytes = (size_t)(n + 1) * row_bytes;
+        if (p->mtab_cap < bytes) {
+            cudaStreamSynchronize(p->stream);
+            dfree(p->mtab);
+            p->mtab = nullptr;
+            p->mtab_cap = 0;
+            rc = dalloc(&p->mtab, bytes, "Dirac mixing rows");
+            if (rc) return rc;
+            p->mtab_cap = bytes;
+        }
+        std::vector<double> packed(bytes / sizeof(double));
+        for (int64_t P = 0; P <= n; ++P) {
+            cd Rn[2][2], Rp[2][2];
+            R(P, Rn);
+            R(P - 1, Rp);
+            cd M[4];
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j) M[2 * i + j] = Rn[i][0] * Rp[0][j] + Rn[i][1] * Rp[1][j];
+            for (int q = 0; q < 4; ++q) {
+                if (p->f64) {
+                    packed[(size_t)P * 8 + 2 * q] = M[q].real();
+                    packed[(size_t)P * 8 + 2 * q + 1] = M[q].imag();
+                } else {
+                    float *f = reinterpret_cast<float *>(packed.data() + (size_t)P * 4);
+                    f[2 * q] = (float)M[q].real();
+                    f[2 * q + 1] = (float)M[q].imag();
+                }
+            }
+        }
+        rc = upload(p, static_cast<double *>(p->mtab), packed.data(), (int64_t)packed.size());
+        if (rc) return rc;
+        Args1D a1{};
+        a1.psi = p->psi;
+        a1.n_rows = 1;
+        a1.n_steps = n;
+        a1.p_begin = 0;
+        a1.p_end = n + 1;
+        a1.p_table0 = 0;
+        a1.tw = p->tw[0];
+        a1.vhalf = p->v_set ? p->vhalf : nullptr;
+        a1.vfull = p->v_set ? p->vfull : nullptr;
+        a1.mtab = p->mtab;
+        a1.dtab = p->dtab;
+        a1.scale_hi = p->scale_hi;
+        a1.scale_lo = p->scale_lo;
+        Bracket br(p, 3);
+        cudaError_t e = p->f64 ? launch_1d_dirac_f64(a1, (int)p->dims[0], p->stream)
+                               : launch_1d_dirac_f32(a1, (int)p->dims[0], p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "1D Dirac step kernel");
+        br.done();
+        return SOP_OK;
+    }
+
     if (p->comps == 4) {
         // ---- Dirac, 2D, component pairs ------------------------------------
         for (int64_t P = 0; P <= n; ++P) {
@@ -729,7 +795,8 @@ int sop_plan_create(sop_plan *out, int ndim, const int64_t *dims, const double *
     if (!dims || !spacing) return fail(SOP_EINVAL, "sop_plan_create: dims or spacing is NULL");
     if (ndim < 1 || ndim > 3) return fail(SOP_EINVAL, "sop_plan_create: ndim must be 1, 2 or 3");
     if (dtype != SOP_C64 && dtype != SOP_C128) return fail(SOP_EINVAL, "sop_plan_create: dtype must be SOP_C64 or SOP_C128");
-    if (components != 1 && components != 4) return fail(SOP_EINVAL, "sop_plan_create: components must be 1 or 4");
+    if (components != 1 && components != 2 && components != 4)
+        return fail(SOP_EINVAL, "sop_plan_create: components must be 1, 2 or 4");
     for (int a = 0; a < ndim; ++a) {
         if (dims[a] <= 0) return fail(SOP_EINVAL, "sop_plan_create: dims must be positive");
         if (!(spacing[a] > 0) || !is_finite(spacing[a])) return fail(SOP_EINVAL, "sop_plan_create: spacing must be finite and > 0");
@@ -739,6 +806,8 @@ int sop_plan_create(sop_plan *out, int ndim, const int64_t *dims, const double *
     }
     if (components == 4 && ndim != 2)
         return fail(SOP_EUNSUPPORTED, "sop_plan_create: the four-component Dirac path supports ndim = 2");
+    if (components == 2 && ndim != 1)
+        return fail(SOP_EUNSUPPORTED, "sop_plan_create: the two-component Dirac path is one-dimensional");
     sop_params prm{1.0, -1.0, 1.0, 137.036};
     if (params) prm = *params;
     if (!(prm.mass > 0) || !(prm.hbar > 0) || !(prm.c > 0) || !is_finite(prm.charge))
@@ -791,7 +860,7 @@ int sop_plan_create(sop_plan *out, int ndim, const int64_t *dims, const double *
         rc = dalloc(&p->tw[a], (size_t)dims[a] * 16, "twiddles");   // float4 hi/lo or double2
         if (!rc && components == 1) rc = dalloc(&p->kin[a], (size_t)dims[a] * p->csz, "kinetic table");
     }
-    if (!rc && components == 4) rc = dalloc(&p->dtab, (size_t)p->npts * 2 * p->csz, "Dirac table");
+    if (!rc && components > 1) rc = dalloc(&p->dtab, (size_t)p->npts * 2 * p->csz, "Dirac table");
     if (!rc) rc = dalloc(&p->theta, (size_t)sum_n * sizeof(double), "angles");
     if (!rc) rc = dalloc(&p->partial, (size_t)reduce_blocks() * sizeof(double), "partials");
     if (!rc) rc = dalloc(&p->result, 4 * sizeof(double), "result");

@@ -98,12 +98,21 @@ struct Args1D {
     const void *ttab;            // kinetic table, or rows of ttab_stride entries per step (velocity gauge)
     int64_t ttab_stride;         // 0: one table for every step; else row (P - p_table0) for step P
     double scale_hi, scale_lo;
+    // Two-component Dirac (1D): mixing rows of 4 complex values (m00, m01,
+    // m10, m11) in the plan's precision per real-space index, row P - p_table0,
+    // and the per-momentum table (cos, sin mc^2/E, sin c p/E, 0) of the
+    // momentum-space factor
+    const void *mtab;
+    const void *dtab;
 };
 
 // Launchers, one translation unit per dtype and axis kind (sop_pass_inst.cu
 // compiled four times, sop_1d_inst.cu twice).  nc: coupled components per
 // pencil (1 or 2).  They return cudaErrorInvalidValue for a size without a
 // kernel.
+// One-dimensional two-component Dirac whole-step kernel (sop_1d_inst.cu).
+cudaError_t launch_1d_dirac_f32(const Args1D &a, int n, cudaStream_t s);
+cudaError_t launch_1d_dirac_f64(const Args1D &a, int n, cudaStream_t s);
 cudaError_t launch_pass_f32_contig(const PassArgs &a, int nc, cudaStream_t s);
 cudaError_t launch_pass_f32_strided(const PassArgs &a, int nc, cudaStream_t s);
 cudaError_t launch_pass_f64_contig(const PassArgs &a, int nc, cudaStream_t s);

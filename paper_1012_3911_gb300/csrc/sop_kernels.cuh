@@ -330,6 +330,87 @@ __global__ void __launch_bounds__(Geometry<N, 1>::T) fso1d_kernel(const __grid_c
     for (int m = 0; m < E; ++m) psi[t + T * m] = v[0][m];
 }
 
+// One-dimensional two-component Dirac equation (end of Sec. 2.3), whole
+// steps on chip: one CTA holds both components of a line in registers.  Per
+// real-space index P: psi <- exp(-i V tau') M_P psi (M_P the merged 2x2
+// mixing of the two adjacent half steps, uniform along the line), then, for
+// P < n_steps, FFT, the per-momentum factor
+//   U = cos(E tau) - i sin(E tau) (c p sigma_x + m c^2 sigma_z) / E
+// (equal to u^dagger diag(e^{-iE tau}, e^{iE tau}) u) with 1/N, inverse FFT.
+template <typename Real, int N>
+__global__ void __launch_bounds__(Geometry<N, 2>::T) fso1d_dirac_kernel(const __grid_constant__ Args1D a) {
+    using C = cplx_t<Real>;
+    using G = Geometry<N, 2>;
+    using Ph = Phase<Real>;
+    constexpr int E = G::E, T = G::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw);
+    const int t = threadIdx.x;
+    C *psi = reinterpret_cast<C *>(a.psi) + blockIdx.x * (int64_t)(2 * N);
+    const C *tw = reinterpret_cast<const C *>(a.tw);
+    const C *vh = reinterpret_cast<const C *>(a.vhalf);
+    const C *vf = reinterpret_cast<const C *>(a.vfull);
+    const C *mt = reinterpret_cast<const C *>(a.mtab);
+    const C *dt2 = reinterpret_cast<const C *>(a.dtab);
+    const Real shi = Real(a.scale_hi), slo = Real(a.scale_lo);
+
+    C v[2][E];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[c][m] = psi[c * N + t + T * m];
+    LayContig<C, G::LR> lay[2];
+    lay[0].p = sm;
+    lay[1].p = sm + (N + (N >> G::LR));
+
+    for (int64_t P = a.p_begin; P < a.p_end; ++P) {
+        const C *vt = (P == 0 || P == a.n_steps) ? vh : vf;
+        const C *mr = mt + (P - a.p_table0) * 4;
+        const C m00 = ldg_c(mr), m01 = ldg_c(mr + 1), m10 = ldg_c(mr + 2), m11 = ldg_c(mr + 3);
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            C u0 = cadd(cmul(m00, v[0][m]), cmul(m01, v[1][m]));
+            C u1 = cadd(cmul(m10, v[0][m]), cmul(m11, v[1][m]));
+            if (vt != nullptr) {
+                const C f = ldg_c(vt + t + T * m);
+                u0 = Ph::apply(u0, f);
+                u1 = Ph::apply(u1, f);
+            }
+            v[0][m] = u0;
+            v[1][m] = u1;
+        }
+        if (P < a.n_steps) {
+            fft_forward<C, N, E, 2>(v, lay, t, tw);
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int k = t + T * m;
+                C q0, q1;
+                if constexpr (sizeof(Real) == 4) {
+                    const float4 q = __ldg(reinterpret_cast<const float4 *>(dt2) + k);
+                    q0 = mk<C>(q.x, q.y);
+                    q1 = mk<C>(q.z, q.w);
+                } else {
+                    q0 = ldg_c(dt2 + 2 * k);
+                    q1 = ldg_c(dt2 + 2 * k + 1);
+                }
+                // q0 = (cos, sin mc^2/E), q1.x = sin c p / E
+                const C u00 = mk<C>(q0.x, -q0.y), u11 = mk<C>(q0.x, q0.y), u01 = mk<C>(Real(0), -q1.x);
+                const C r0 = cadd(cmul(u00, v[0][m]), cmul(u01, v[1][m]));
+                const C r1 = cadd(cmul(u01, v[0][m]), cmul(u11, v[1][m]));
+                v[0][m] = scale2(r0, shi, slo);
+                v[1][m] = scale2(r1, shi, slo);
+            }
+            __syncthreads();
+            fft_dir<C, N, E, 2>(v, lay, t, tw, +1);
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int m = 0; m < E; ++m) psi[c * N + t + T * m] = v[c][m];
+}
+
 // ---------------------------------------------------------------------------
 // Launch helpers
 // ---------------------------------------------------------------------------
@@ -352,6 +433,19 @@ cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t s) {
     dim3 grid((unsigned)blocks, 1, NC == 2 ? 2 : 1);
     dim3 block = CONTIG ? dim3(Cfg::T, Cfg::WP, 1) : dim3(Cfg::WP, Cfg::T, 1);
     kern<<<grid, block, Cfg::SMEM, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename Real, int N> cudaError_t launch_1d_dirac_t(const Args1D &a, cudaStream_t s) {
+    using G = Geometry<N, 2>;
+    constexpr size_t SMEM = G::P.S > 1 ? (size_t)(N + (N >> G::LR)) * 2 * 2 * sizeof(Real) : 0;
+    auto kern = fso1d_dirac_kernel<Real, N>;
+    if (SMEM > 48 * 1024) {
+        cudaError_t e = ensure_smem_attr(reinterpret_cast<const void *>(kern), (int)SMEM);
+        if (e != cudaSuccess) return e;
+    }
+    if (a.n_rows <= 0) return cudaSuccess;
+    kern<<<(unsigned)a.n_rows, G::T, SMEM, s>>>(a);
     return cudaGetLastError();
 }
 

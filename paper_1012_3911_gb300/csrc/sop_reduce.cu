@@ -67,7 +67,8 @@ struct KGeom {
 
 // Schroedinger: sum_k |p_k|^2/(2m) |psi~_k|^2.
 // Dirac (2D, four components): sum_k psi~^dag (c alpha.p + m c^2 beta) psi~,
-// written out on the coupled pairs (1,4) and (2,3).
+// written out on the coupled pairs (1,4) and (2,3); 1D, two components:
+// alpha_1 = sigma_x, beta = sigma_z.
 template <typename C>
 __global__ void __launch_bounds__(kThreads) k_energy_t(const C *pt, KGeom g, const double *pgrid, int comps,
                                                         double mass, double c, double *partial) {
@@ -90,6 +91,13 @@ __global__ void __launch_bounds__(kThreads) k_energy_t(const C *pt, KGeom g, con
             const double x = (double)z.x, y = (double)z.y;
             const double p2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
             acc = fma(p2 / (2.0 * mass), fma(x, x, y * y), acc);
+        } else if (comps == 2) {
+            // 1D: H = c p sigma_x + m c^2 sigma_z
+            const C z0 = pt[k], z1 = pt[npts + k];
+            const double n0 = (double)z0.x * z0.x + (double)z0.y * z0.y;
+            const double n1 = (double)z1.x * z1.x + (double)z1.y * z1.y;
+            const double sr = (double)z0.x * z1.x + (double)z0.y * z1.y;   // Re conj(z0) z1
+            acc += mass * c * c * (n0 - n1) + 2.0 * c * p[0] * sr;
         } else {
             const C z0 = pt[k], z1 = pt[npts + k], z2 = pt[2 * npts + k], z3 = pt[3 * npts + k];
             const double mc2 = mass * c * c;

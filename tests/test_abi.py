@@ -51,7 +51,8 @@ def test_version_and_empty_error(lib):
     ((18, 16), 1, sop.SOP_EUNSUPPORTED),   # 9 = 3^2 needs two radix-3 stages
     ((8192,), 1, sop.SOP_EUNSUPPORTED),    # above 4096
     ((16, 16, 16, 16), 1, sop.SOP_EINVAL), # ndim 4
-    ((16, 16), 2, sop.SOP_EINVAL),         # components must be 1 or 4
+    ((16, 16), 3, sop.SOP_EINVAL),         # components must be 1, 2 or 4
+    ((16, 16), 2, sop.SOP_EUNSUPPORTED),   # two-component Dirac needs ndim = 1
     ((16,), 4, sop.SOP_EUNSUPPORTED),      # Dirac needs ndim = 2
     ((16, 16, 16), 4, sop.SOP_EUNSUPPORTED),
 ])
