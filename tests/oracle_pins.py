@@ -409,6 +409,61 @@ def pin_free_dirac_exact(orc):
     assert relerr(out, _free_dirac_exact(psi0, dims, sp, tau * n)) < 1e-12
 
 
+def _per_momentum_3d(psi0, dims, sp, fn):
+    """Apply the 4x4 matrix fn(p) to every momentum of a 3D spinor (NumPy FFT)."""
+    st = np.stack([np.fft.fftn(psi0[k]) for k in range(4)])
+    P = np.meshgrid(*[wl.momenta(m, h) for m, h in zip(dims, sp)][::-1], indexing="ij")[::-1]
+    for idx in np.ndindex(*st.shape[1:]):
+        p = np.array([P[0][idx], P[1][idx], P[2][idx]])
+        st[(slice(None),) + idx] = fn(p) @ st[(slice(None),) + idx]
+    return np.stack([np.fft.ifftn(st[k]) for k in range(4)])
+
+
+def pin_free_dirac_exact_3d(orc):
+    """3D, V = 0, A = 0: per momentum psi~(t) = expm(-i t H(p)) psi~(0) with the
+    textbook H including alpha_3 (scipy expm), random spinor."""
+    dims, sp = (8, 12, 8), (0.06, 0.05, 0.07)
+    psi0 = wl.random_state((4,) + dims[::-1], 63)
+    tau, n = 1.5e-4, 4
+    out = orc.dirac_propagate(psi0, None, sp, tau, n)
+    ref = _per_momentum_3d(psi0, dims, sp, lambda p: scipy.linalg.expm(-1j * tau * n * textbook_h(p)))
+    assert relerr(out, ref) < 1e-12
+
+
+def pin_dirac_uniform_A_second_order_3d(orc):
+    """3D, constant A with all three components, V = 0: the split converges
+    at second order to expm(-i t H(p - qA)) (q = -1)."""
+    c = 10.0
+    dims, sp = (8, 8, 12), (0.4, 0.4, 0.3)
+    psi0 = wl.random_smooth_state(dims, sp, 64, comps=4)
+    A = np.array([0.7, -0.5, 0.4])
+    t = 0.15
+    ref = _per_momentum_3d(psi0, dims, sp, lambda p: scipy.linalg.expm(-1j * t * textbook_h(p + A, 1.0, c)))
+    errs = []
+    for n in (16, 32):
+        out = orc.dirac_propagate(psi0, None, sp, t / n, n, np.tile(A, (n, 1)), c=c)
+        errs.append(relerr(out, ref))
+    assert errs[0] < 5e-2, errs
+    assert 3.5 < errs[0] / errs[1] < 4.5, errs
+
+
+def pin_dirac_energy_3d(orc):
+    """<H> of a 3D spinor against (dV/N) sum_k psi~^dag H(p) psi~ + dV sum V |psi|^2."""
+    dims, sp = (8, 12, 8), (0.1, 0.08, 0.12)
+    psi = wl.random_state((4,) + dims[::-1], 65, sp)
+    V = wl.random_potential(dims, 66, 2.0)
+    st = np.stack([np.fft.fftn(psi[k]) for k in range(4)])
+    P = np.meshgrid(*[wl.momenta(m, h) for m, h in zip(dims, sp)][::-1], indexing="ij")[::-1]
+    t = 0.0
+    for idx in np.ndindex(*st.shape[1:]):
+        v = st[(slice(None),) + idx]
+        t += np.vdot(v, textbook_h((P[0][idx], P[1][idx], P[2][idx])) @ v).real
+    dV = float(np.prod(sp))
+    N = int(np.prod(dims))
+    ref = dV / N * t + dV * np.sum(V * np.sum(np.abs(psi) ** 2, axis=0))
+    assert abs(orc.energy(psi, V, sp, 4) - ref) < 1e-10 * abs(ref)
+
+
 def pin_dirac_constant_potential_phase(orc):
     """A constant V0 with A = 0 only adds the global phase exp(-i V0 t) to the
     free Dirac evolution (Eqs. 21-22: the scalar factor commutes)."""
@@ -601,7 +656,8 @@ ALL_PINS = [
     pin_shift_covariance, pin_field_kick_plane_wave, pin_velocity_gauge_plane_waves,
     pin_velocity_gauge_lattice_shift, pin_dirac1d_u_diagonalises, pin_dirac1d_free_exact,
     pin_dirac1d_constant_potential_phase, pin_dirac1d_norm_and_reversibility, pin_dirac1d_equals_2d_pair,
-    pin_dirac1d_uniform_A_second_order, pin_dirac1d_energy, pin_ehrenfest_field, pin_schrodinger_energy,
+    pin_dirac1d_uniform_A_second_order, pin_dirac1d_energy, pin_free_dirac_exact_3d,
+    pin_dirac_uniform_A_second_order_3d, pin_dirac_energy_3d, pin_ehrenfest_field, pin_schrodinger_energy,
     pin_dirac_algebra, pin_dirac_u_diagonalises, pin_dirac_kinetic_expm, pin_dirac_mixing_expm,
     pin_free_dirac_exact, pin_dirac_constant_potential_phase, pin_dirac_norm_and_reversibility, pin_dirac_uniform_A_second_order,
     pin_dirac_velocity, pin_dirac_energy,

@@ -47,6 +47,8 @@ MUTANTS = [
      [pins.pin_dirac1d_u_diagonalises, pins.pin_dirac1d_free_exact]),
     ("dirac1d_energy_u_not_h", "dirac1d_h(p[0], mass, c, H);", "dirac1d_u(p[0], mass, c, H);",
      [pins.pin_dirac1d_energy]),
+    ("alpha3_sign", "alpha[2][0][2] = 1; alpha[2][1][3] = -1;", "alpha[2][0][2] = -1; alpha[2][1][3] = 1;",
+     [pins.pin_free_dirac_exact_3d, pins.pin_dirac_uniform_A_second_order_3d]),
     ("lattice_origin", "return -0.5 * (double)n * h + (double)j * h;",
      "return -0.5 * (double)n * h + (double)(j + 1) * h;", [pins.pin_field_kick_plane_wave]),
     ("dirac_u_not_adjoint", "for (int k = 0; k < 4; ++k) s += conj(u[k][i]) * w[k];",
