@@ -279,6 +279,7 @@ def main():
     spectral = None
     velocity = None
     dirac1d = None
+    dirac3d = None
     if args.batched and rank == 0:
         ws = wl.config5(64, n_steps=args.batch_steps)
         npts5 = sum(x.npoints for x in ws)
@@ -414,6 +415,39 @@ def main():
                                f"A_1 = 20 sin^2 cos 2t, dt 1e-4, {T1} steps, one CTA keeps the line on chip",
                    "us_per_step": td / T1 * 1e6}
         qd.close()
+        # three-dimensional four-component Dirac: 128^3 on [-4,4)^3, soft core,
+        # A with three components; 4x4 factors as streaming passes between the
+        # transforms of the four components
+        n3, T3 = 128, 50
+        h3 = 8.0 / n3
+        X3 = wl.mesh((n3, n3, n3), (h3, h3, h3))
+        t3 = (np.arange(T3) + 0.5) * 1e-4
+        A3 = np.stack([20.0 * np.cos(2.0 * t3), 5.0 * np.sin(2.0 * t3), 2.0 * np.ones_like(t3)], axis=1)
+        scal = wl.gaussian((n3, n3, n3), (h3, h3, h3), (0.0, 0.0, 0.0), 0.5, (50.0, 0.0, 0.0))
+        psi3 = wl.dirac_positive_spin_up(scal, (n3, n3, n3), (h3, h3, h3))
+        q3 = sop.Propagator((n3, n3, n3), (h3, h3, h3), 4, "c64")
+        q3.set_potential(-1.0 / np.sqrt(X3[0] ** 2 + X3[1] ** 2 + X3[2] ** 2 + 0.01))
+        q3.set_state(torch.from_numpy(psi3))
+        del X3, scal, psi3
+        q3.step(3, 1e-4, A3[:3])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        q3.step(T3, 1e-4, A3)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t3d = e0.elapsed_time(e1) * 1e-3
+        npt3 = n3 ** 3
+        # streamed bytes per step: 6 transform passes + 2 factor passes over 4 components
+        # (read + write, 8 B each), the per-momentum table (32 B) and FP32 V phase (8 B)
+        design3 = 8 * 2 * 4 * 8 * npt3 + 32 * npt3 + 8 * npt3
+        dirac3d = {"value": npt3 * T3 / t3d, "unit": UNIT, "dtype": "f32",
+                   "workload": f"3D four-component Dirac, {n3}^3 on [-4,4)^3, soft core (a^2 0.01), "
+                               f"A = (20 cos 2t, 5 sin 2t, 2), dt 1e-4, {T3} steps",
+                   "us_per_step": t3d / T3 * 1e6,
+                   "design_bytes_per_step": design3,
+                   "design_frac_of_peak": design3 / (t3d / T3) / 1e9 / measured_peaks()[0]}
+        q3.close()
+        torch.cuda.empty_cache()
 
     # ---- FP64 sample, same lattice -----------------------------------------
     fp64 = None
@@ -508,7 +542,7 @@ def main():
                              "within a step",
                        "parallelism": f"replicas x{world} (independent problems, no data-path collective)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "fp64": fp64, "batched": batched, "adjoint": adjoint, "spectral": spectral, "velocity_gauge": velocity, "dirac1d": dirac1d, "err_vs_oracle": err, "clocks": clocks,
+            "fp64": fp64, "batched": batched, "adjoint": adjoint, "spectral": spectral, "velocity_gauge": velocity, "dirac1d": dirac1d, "dirac3d": dirac3d, "err_vs_oracle": err, "clocks": clocks,
         }
         s = json.dumps(line)
         print(s, flush=True)

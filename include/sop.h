@@ -75,7 +75,9 @@ typedef struct {
  *   dims       ndim sides in axis order (dims[0] = n_x, contiguous); each
  *              side must be 2^a * 3^b with a >= 2, b <= 1 and 8 <= side <= 4096.
  *   spacing    ndim lattice spacings (> 0).
- *   components 1 (Schroedinger, Sec. 2.2), 4 (Dirac, Sec. 2.3, ndim = 2) or
+ *   components 1 (Schroedinger, Sec. 2.2), 4 (Dirac, Sec. 2.3, ndim = 2 or 3;
+ *              in 3D the 4x4 factors couple all components and run as
+ *              separate streaming passes between the transforms) or
  *              2 (the one-dimensional two-component Dirac equation at the
  *              end of Sec. 2.3, ndim = 1, alpha_1 = sigma_x, beta = sigma_z;
  *              field_samples are A_1, one per step).

@@ -36,6 +36,7 @@ UNITS = [
     ("api", "sop_api.cu", []),
     ("noalloc", "sop_noalloc.cu", []),
     ("adjoint", "sop_adjoint.cu", []),
+    ("dirac3d", "sop_dirac3d.cu", []),
 ]
 
 

@@ -452,7 +452,10 @@ int ensure_tables(sop_plan p, double dt) {
         br.done(p->ndim);
     } else {
         Bracket br(p, 4);
-        e = build_dirac_table(p->dtab, p->dims, p->h, p->prm.mass, p->prm.c, hbar, dt, p->f64, p->stream);
+        e = p->ndim == 3 ? build_dirac3_table(p->dtab, p->dims, p->h, p->prm.mass, p->prm.c, hbar, dt, p->f64,
+                                              p->stream)
+                         : build_dirac_table(p->dtab, p->dims, p->h, p->prm.mass, p->prm.c, hbar, dt, p->f64,
+                                             p->stream);
         if (e != cudaSuccess) return cuda_fail(e, "build_dirac_table");
         br.done();
     }
@@ -621,6 +624,93 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
                                : launch_1d_dirac_f32(a1, (int)p->dims[0], p->stream);
         if (e != cudaSuccess) return cuda_fail(e, "1D Dirac step kernel");
         br.done();
+        return SOP_OK;
+    }
+
+    if (p->comps == 4 && nd == 3) {
+        // ---- Dirac, 3D: the 4x4 factors couple all components ---------------
+        // Per real-space index P: exp(-i V tau') M_P with M_P = R(A_P) R(A_{P-1}),
+        // then (P < n) the forward transforms of all four components along x,
+        // y, z, the momentum-space factor, the inverse transforms.
+        cd al[3][4][4];
+        for (int a = 0; a < 3; ++a)
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) al[a][i][j] = 0.0;
+        al[0][0][3] = al[0][1][2] = al[0][2][1] = al[0][3][0] = 1.0;   // alpha_1 (Dirac representation)
+        al[1][0][3] = cd(0, -1);                                        // alpha_2
+        al[1][1][2] = cd(0, 1);
+        al[1][2][1] = cd(0, -1);
+        al[1][3][0] = cd(0, 1);
+        al[2][0][2] = 1.0;                                              // alpha_3
+        al[2][1][3] = -1.0;
+        al[2][2][0] = 1.0;
+        al[2][3][1] = -1.0;
+        // R(A) = cos th + i sin th sum_a (Abar_a/Abar) alpha_a with Abar_a = A_a tau and
+        // th = q c Abar / (2 hbar) (Eq. 26 with delta = 1/2; identity for A = 0)
+        auto R = [&](int64_t s, cd M[4][4]) {
+            double Ab[3] = {0, 0, 0}, mag = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                Ab[a] = sample(s, a) * dt;
+                mag += Ab[a] * Ab[a];
+            }
+            mag = std::sqrt(mag);
+            const double th = 0.5 * p->prm.charge * p->prm.c * mag / hbar;
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) {
+                    cd v = (i == j) ? cd(std::cos(th), 0.0) : cd(0.0, 0.0);
+                    if (mag > 0)
+                        for (int a = 0; a < 3; ++a) v += cd(0.0, std::sin(th)) * (Ab[a] / mag) * al[a][i][j];
+                    M[i][j] = v;
+                }
+        };
+        for (int64_t P = 0; P <= n; ++P) {
+            cd Rn[4][4], Rp[4][4];
+            R(P, Rn);
+            R(P - 1, Rp);
+            double Md[32];
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) {
+                    cd v = 0.0;
+                    for (int k = 0; k < 4; ++k) v += Rn[i][k] * Rp[k][j];
+                    Md[2 * (4 * i + j)] = v.real();
+                    Md[2 * (4 * i + j) + 1] = v.imag();
+                }
+            const bool smp = step_sampled(p, P);
+            {
+                Bracket br(p, 0, smp);
+                cudaError_t e = launch_dirac3_real(p->psi, p->npts, p->v_set ? ((P == 0 || P == n) ? p->vhalf : p->vfull)
+                                                                             : nullptr,
+                                                   Md, p->f64, p->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "3D Dirac real-space factor");
+                br.done();
+            }
+            if (P == n) break;
+            for (int ax = 0; ax < 3; ++ax) {
+                PassArgs a;
+                base_args(p, a, p->psi, ax);
+                a.n_batch = 4;
+                a.pre = -1;
+                a.op = OP_NONE;
+                rc = run_pass(p, a, 1, 2, "3D Dirac forward transform", smp);
+                if (rc) return rc;
+            }
+            {
+                Bracket br(p, 1, smp);
+                cudaError_t e = launch_dirac3_kinetic(p->psi, p->npts, p->dtab, p->scale_hi, p->scale_lo, p->f64,
+                                                      p->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "3D Dirac momentum-space factor");
+                br.done();
+            }
+            for (int ax = 2; ax >= 0; --ax) {
+                PassArgs a;
+                base_args(p, a, p->psi, ax);
+                a.n_batch = 4;
+                a.pre = +1;
+                a.op = OP_NONE;
+                rc = run_pass(p, a, 1, 2, "3D Dirac inverse transform", smp);
+                if (rc) return rc;
+            }
+        }
         return SOP_OK;
     }
 
@@ -804,8 +894,8 @@ int sop_plan_create(sop_plan *out, int ndim, const int64_t *dims, const double *
             return fail(SOP_EUNSUPPORTED, "sop_plan_create: side " + std::to_string(dims[a]) +
                                               " is not 2^a*3^b with a>=2, b<=1, 8<=n<=4096");
     }
-    if (components == 4 && ndim != 2)
-        return fail(SOP_EUNSUPPORTED, "sop_plan_create: the four-component Dirac path supports ndim = 2");
+    if (components == 4 && ndim == 1)
+        return fail(SOP_EUNSUPPORTED, "sop_plan_create: the four-component Dirac path needs ndim = 2 or 3");
     if (components == 2 && ndim != 1)
         return fail(SOP_EUNSUPPORTED, "sop_plan_create: the two-component Dirac path is one-dimensional");
     sop_params prm{1.0, -1.0, 1.0, 137.036};
@@ -860,7 +950,8 @@ int sop_plan_create(sop_plan *out, int ndim, const int64_t *dims, const double *
         rc = dalloc(&p->tw[a], (size_t)dims[a] * 16, "twiddles");   // float4 hi/lo or double2
         if (!rc && components == 1) rc = dalloc(&p->kin[a], (size_t)dims[a] * p->csz, "kinetic table");
     }
-    if (!rc && components > 1) rc = dalloc(&p->dtab, (size_t)p->npts * 2 * p->csz, "Dirac table");
+    if (!rc && components > 1)   // per momentum: 4 reals (1D, 2D) or 8 (3D)
+        rc = dalloc(&p->dtab, (size_t)p->npts * (ndim == 3 ? 4 : 2) * p->csz, "Dirac table");
     if (!rc) rc = dalloc(&p->theta, (size_t)sum_n * sizeof(double), "angles");
     if (!rc) rc = dalloc(&p->partial, (size_t)reduce_blocks() * sizeof(double), "partials");
     if (!rc) rc = dalloc(&p->result, 4 * sizeof(double), "result");

@@ -1,0 +1,154 @@
+// sop_dirac3d.cu -- pointwise factors of the three-dimensional four-component
+// Dirac step (Sec. 2.3 with d = 3).
+//
+// In three dimensions alpha_3 couples components (1,3) and (2,4) and
+// alpha_1, alpha_2 couple (1,4) and (2,3), so neither factor splits into
+// component pairs.  The step runs the three transforms of each component as
+// separate pencil passes (components as a batch) and applies the two 4x4
+// factors here, one streaming pass over the four components each:
+//   real space:      psi <- exp(-i V tau') M psi, M the merged mixing of the
+//                    adjacent half steps (Eqs. 21-26), uniform in space;
+//   momentum space:  psi~ <- (1/N) [cos(E tau) - i sin(E tau) H(p)/E] psi~,
+//                    H = c alpha.p + m c^2 beta (the closed form of Eq. 33).
+#include "sop_kernels.cuh"
+#include "sop_internal.h"
+
+namespace sop {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kBlocks = 152 * 8;
+
+__device__ __forceinline__ double lat_p(int64_t n, double h, int64_t k, double hbar) {
+    const int64_t kap = (2 * k < n) ? k : k - n;
+    return hbar * 6.283185307179586476925286766559 * (double)kap / ((double)n * h);
+}
+
+// Entry k (x fastest): (cos th, sin th mc^2/E, sin th c p_x/E, sin th c p_y/E,
+// sin th c p_z/E, 0, 0, 0) with th = E tau / hbar, formed in FP64 and rounded
+// to the plan's precision.
+__global__ void k_dirac3_table(void *out, int64_t nx, int64_t ny, int64_t nz, double hx, double hy, double hz,
+                               double mass, double c, double hbar, double tau, bool f64) {
+    const int64_t total = nx * ny * nz;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t kx = k % nx, r = k / nx, ky = r % ny, kz = r / ny;
+        const double px = lat_p(nx, hx, kx, hbar), py = lat_p(ny, hy, ky, hbar), pz = lat_p(nz, hz, kz, hbar);
+        const double mc2 = mass * c * c;
+        const double E = sqrt(mc2 * mc2 + (px * px + py * py + pz * pz) * c * c);
+        double s, co;
+        sincos(E * tau / hbar, &s, &co);
+        const double q[5] = {co, s * mc2 / E, s * c * px / E, s * c * py / E, s * c * pz / E};
+        if (f64) {
+            double *o = reinterpret_cast<double *>(out) + 8 * k;
+            for (int i = 0; i < 5; ++i) o[i] = q[i];
+            o[5] = o[6] = o[7] = 0.0;
+        } else {
+            float4 *o = reinterpret_cast<float4 *>(out) + 2 * k;
+            o[0] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
+            o[1] = make_float4((float)q[4], 0.f, 0.f, 0.f);
+        }
+    }
+}
+
+template <typename Real> struct Mix4 {
+    cplx_t<Real> m[16];   // row-major 4x4
+};
+
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) k_dirac3_real(cplx_t<Real> *psi, int64_t npts, const cplx_t<Real> *vtab,
+                                                          Mix4<Real> M) {
+    using C = cplx_t<Real>;
+    using Ph = Phase<Real>;
+    for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < npts; j += (int64_t)gridDim.x * kThreads) {
+        C v[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = __ldcg(psi + c * npts + j);
+        const C f = vtab ? __ldcg(vtab + j) : Ph::one();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            C w = cmul(M.m[4 * i], v[0]);
+#pragma unroll
+            for (int k = 1; k < 4; ++k) w = cadd(w, cmul(M.m[4 * i + k], v[k]));
+            if (vtab) w = Ph::apply(w, f);
+            __stcg(psi + i * npts + j, w);
+        }
+    }
+}
+
+// U = cos - i sin H/E with H/E = [[mu, 0, kz, km], [0, mu, kp, -kz],
+// [kz, km, -mu, 0], [kp, -kz, 0, -mu]], kp = c(p_x + i p_y)/E, km = conj(kp),
+// kz = c p_z / E, mu = m c^2 / E; then 1/N.
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) k_dirac3_kinetic(cplx_t<Real> *psi, int64_t npts, const Real *tab,
+                                                             Real shi, Real slo) {
+    using C = cplx_t<Real>;
+    for (int64_t k = (int64_t)blockIdx.x * kThreads + threadIdx.x; k < npts; k += (int64_t)gridDim.x * kThreads) {
+        Real co, sm, sx, sy, sz;
+        if constexpr (sizeof(Real) == 4) {
+            const float4 a = __ldcg(reinterpret_cast<const float4 *>(tab) + 2 * k);
+            const float4 b = __ldcg(reinterpret_cast<const float4 *>(tab) + 2 * k + 1);
+            co = a.x; sm = a.y; sx = a.z; sy = a.w; sz = b.x;
+        } else {
+            const double2 a = __ldcg(reinterpret_cast<const double2 *>(tab) + 4 * k);
+            const double2 b = __ldcg(reinterpret_cast<const double2 *>(tab) + 4 * k + 1);
+            const double2 d = __ldcg(reinterpret_cast<const double2 *>(tab) + 4 * k + 2);
+            co = a.x; sm = a.y; sx = b.x; sy = b.y; sz = d.x;
+        }
+        C v[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = __ldcg(psi + c * npts + k);
+        const C dm = mk<C>(co, -sm), dp = mk<C>(co, sm);      // cos -+ i sin mu
+        const C uz = mk<C>(Real(0), -sz), vz = mk<C>(Real(0), sz);   // -i sin kz, +i sin kz
+        const C um = mk<C>(-sy, -sx);                          // -i sin km
+        const C up = mk<C>(sy, -sx);                           // -i sin kp
+        C r[4];
+        r[0] = cadd(cmul(dm, v[0]), cadd(cmul(uz, v[2]), cmul(um, v[3])));
+        r[1] = cadd(cmul(dm, v[1]), cadd(cmul(up, v[2]), cmul(vz, v[3])));
+        r[2] = cadd(cmul(uz, v[0]), cadd(cmul(um, v[1]), cmul(dp, v[2])));
+        r[3] = cadd(cmul(up, v[0]), cadd(cmul(vz, v[1]), cmul(dp, v[3])));
+#pragma unroll
+        for (int c = 0; c < 4; ++c) __stcg(psi + c * npts + k, scale2(r[c], shi, slo));
+    }
+}
+
+template <typename Real>
+cudaError_t dirac3_real_t(void *psi, int64_t npts, const void *vtab, const double *Md, cudaStream_t s) {
+    Mix4<Real> M;   // (host code: no device helpers)
+    for (int q = 0; q < 16; ++q) {
+        M.m[q].x = (Real)Md[2 * q];
+        M.m[q].y = (Real)Md[2 * q + 1];
+    }
+    k_dirac3_real<Real><<<kBlocks, kThreads, 0, s>>>(static_cast<cplx_t<Real> *>(psi), npts,
+                                                      static_cast<const cplx_t<Real> *>(vtab), M);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t build_dirac3_table(void *out, const int64_t *dims, const double *h, double mass, double c, double hbar,
+                               double dt, bool f64, cudaStream_t s) {
+    k_dirac3_table<<<kBlocks, kThreads, 0, s>>>(out, dims[0], dims[1], dims[2], h[0], h[1], h[2], mass, c, hbar, dt,
+                                                f64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dirac3_real(void *psi, int64_t npts, const void *vtab, const double *M, bool f64,
+                               cudaStream_t s) {
+    return f64 ? dirac3_real_t<double>(psi, npts, vtab, M, s) : dirac3_real_t<float>(psi, npts, vtab, M, s);
+}
+
+cudaError_t launch_dirac3_kinetic(void *psi, int64_t npts, const void *tab, double shi, double slo, bool f64,
+                                  cudaStream_t s) {
+    if (f64)
+        k_dirac3_kinetic<double><<<kBlocks, kThreads, 0, s>>>(static_cast<double2 *>(psi), npts,
+                                                               static_cast<const double *>(tab), shi, slo);
+    else
+        k_dirac3_kinetic<float><<<kBlocks, kThreads, 0, s>>>(static_cast<float2 *>(psi), npts,
+                                                              static_cast<const float *>(tab), (float)shi,
+                                                              (float)slo);
+    return cudaGetLastError();
+}
+
+}  // namespace sop

@@ -110,6 +110,16 @@ struct Args1D {
 // compiled four times, sop_1d_inst.cu twice).  nc: coupled components per
 // pencil (1 or 2).  They return cudaErrorInvalidValue for a size without a
 // kernel.
+// Three-dimensional four-component Dirac (sop_dirac3d.cu): the per-momentum
+// table (8 reals per momentum in the plan's precision), the real-space factor
+// exp(-i V tau') M (M: 16 complex FP64 values, row-major; vtab may be null) and
+// the momentum-space factor with 1/N, each one pass over the four components.
+cudaError_t build_dirac3_table(void *out, const int64_t *dims, const double *h, double mass, double c, double hbar,
+                               double dt, bool f64, cudaStream_t s);
+cudaError_t launch_dirac3_real(void *psi, int64_t npts, const void *vtab, const double *M, bool f64,
+                               cudaStream_t s);
+cudaError_t launch_dirac3_kinetic(void *psi, int64_t npts, const void *tab, double shi, double slo, bool f64,
+                                  cudaStream_t s);
 // One-dimensional two-component Dirac whole-step kernel (sop_1d_inst.cu).
 cudaError_t launch_1d_dirac_f32(const Args1D &a, int n, cudaStream_t s);
 cudaError_t launch_1d_dirac_f64(const Args1D &a, int n, cudaStream_t s);

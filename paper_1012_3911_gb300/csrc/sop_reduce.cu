@@ -110,8 +110,10 @@ __global__ void __launch_bounds__(kThreads) k_energy_t(const C *pt, KGeom g, con
             const double si = (double)z0.x * z3.y - (double)z0.y * z3.x;
             const double ur = (double)z1.x * z2.x + (double)z1.y * z2.y;
             const double ui = (double)z1.x * z2.y - (double)z1.y * z2.x;
-            // Re[(p_x - i p_y) s] = p_x sr + p_y si ; Re[(p_x + i p_y) u] = p_x ur - p_y ui
-            const double off = 2.0 * c * (p[0] * sr + p[1] * si + p[0] * ur - p[1] * ui);
+            // Re[(p_x - i p_y) s] = p_x sr + p_y si ; Re[(p_x + i p_y) u] = p_x ur - p_y ui;
+            // alpha_3 (3D): p_z Re[conj(z0) z2 - conj(z1) z3]
+            const double zr = (double)z0.x * z2.x + (double)z0.y * z2.y - (double)z1.x * z3.x - (double)z1.y * z3.y;
+            const double off = 2.0 * c * (p[0] * sr + p[1] * si + p[0] * ur - p[1] * ui + p[2] * zr);
             acc += mc2 * (n0 + n1 - n2 - n3) + off;
         }
     }

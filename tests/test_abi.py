@@ -53,8 +53,8 @@ def test_version_and_empty_error(lib):
     ((16, 16, 16, 16), 1, sop.SOP_EINVAL), # ndim 4
     ((16, 16), 3, sop.SOP_EINVAL),         # components must be 1, 2 or 4
     ((16, 16), 2, sop.SOP_EUNSUPPORTED),   # two-component Dirac needs ndim = 1
-    ((16,), 4, sop.SOP_EUNSUPPORTED),      # Dirac needs ndim = 2
-    ((16, 16, 16), 4, sop.SOP_EUNSUPPORTED),
+    ((16,), 4, sop.SOP_EUNSUPPORTED),      # four-component Dirac needs ndim = 2 or 3
+    ((16, 16, 16), 2, sop.SOP_EUNSUPPORTED),
 ])
 def test_create_rejects_before_touching_the_gpu(lib, dims, comps, status):
     out = ctypes.c_void_p()
