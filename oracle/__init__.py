@@ -75,6 +75,9 @@ def _load():
         lib.orc_dirac_propagate.restype = ctypes.c_int
         lib.orc_dirac_alpha_beta.argtypes = [P]
         lib.orc_dirac_u.argtypes = [dp, ctypes.c_int, d, d, P]
+        lib.orc_dirac_propagate_profile.argtypes = [P, P, ctypes.c_int, i64p, dp, d, d, d, d, d,
+                                                    ctypes.c_int64, P]
+        lib.orc_dirac_propagate_profile.restype = ctypes.c_int
         lib.orc_dirac1d_u.argtypes = [d, d, d, P]
         lib.orc_dirac1d_h.argtypes = [d, d, d, P]
         lib.orc_dirac1d_propagate.argtypes = [P, P, ctypes.c_int64, d, d, d, d, d, d, ctypes.c_int64, P]
@@ -237,6 +240,31 @@ def dirac_propagate(psi, V, spacing, dt: float, n_steps: int, field=None,
         fp = fc.ctypes.data
     rc = _load().orc_dirac_propagate(y.ctypes.data, Vp, ndim, _dims(sp), _dp(spacing), mass,
                                      charge, hbar, c, float(dt), int(n_steps), fp)
+    if rc != 0:
+        raise ValueError("unsupported shape")
+    return y
+
+
+def dirac_propagate_profile(psi, V, spacing, dt: float, n_steps: int, field,
+                            mass: float = 1.0, charge: float = -1.0, hbar: float = 1.0,
+                            c: float = 137.036) -> np.ndarray:
+    """As dirac_propagate, for a vector potential that varies along x_1:
+    ``field`` has shape (n_steps, n_x, ndim), A at each step midpoint and
+    lattice column of axis 0 (the mixing of Eq. 26 per column)."""
+    y = _c128(psi).copy()
+    if y.shape[0] != 4:
+        raise ValueError("Dirac spinor needs 4 components on axis 0")
+    sp = y.shape[1:]
+    ndim = len(sp)
+    Vp = None
+    if V is not None:
+        Vc = _f64(V)
+        if Vc.shape != sp:
+            raise ValueError("V must have the spatial shape of psi")
+        Vp = Vc.ctypes.data
+    fc = _f64(field).reshape(int(n_steps), sp[-1], ndim)
+    rc = _load().orc_dirac_propagate_profile(y.ctypes.data, Vp, ndim, _dims(sp), _dp(spacing), mass,
+                                             charge, hbar, c, float(dt), int(n_steps), fc.ctypes.data)
     if rc != 0:
         raise ValueError("unsupported shape")
     return y

@@ -509,6 +509,47 @@ int orc_dirac_propagate(cplx *psi, const double *V, int ndim, const int64_t *dim
     return 0;
 }
 
+/* A vector potential that varies along x_1 (a plane-wave laser pulse
+ * travelling along x_1, the scattering example of the paper's results): the
+ * mixing of Eq. 26 then differs per lattice column, with Abar(x) = A(x_1, t)
+ * tau.  field: n_steps x dims[0] x ndim samples, A at the step midpoint and
+ * lattice column i of axis 0. */
+int orc_dirac_propagate_profile(cplx *psi, const double *V, int ndim, const int64_t *dims,
+                                const double *h, double mass, double charge, double hbar, double c,
+                                double tau, int64_t n_steps, const double *field) {
+    if (ndim < 2 || ndim > 3 || !field) return -1;
+    for (int a = 0; a < ndim; ++a)
+        if (!orc_size_ok(dims[a])) return -1;
+    const int64_t N = npoints(ndim, dims), nx = dims[0];
+    cplx(*R)[4][4] = (cplx(*)[4][4])malloc(sizeof(cplx) * 16 * (size_t)nx);
+    for (int64_t n = 0; n < n_steps; ++n) {
+        for (int64_t i = 0; i < nx; ++i)
+            dirac_mixing(field + (n * nx + i) * ndim, ndim, charge, c, hbar, tau, 0.5, R[i]);
+        for (int half = 0; half < 2; ++half) {
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+            for (int64_t j = 0; j < N; ++j) {
+                const cplx(*Rj)[4] = (const cplx(*)[4])R[j % nx];
+                cplx v[4], w[4];
+                for (int cc = 0; cc < 4; ++cc) v[cc] = psi[cc * N + j];
+                for (int r = 0; r < 4; ++r) {
+                    cplx s = 0;
+                    for (int k = 0; k < 4; ++k) s += Rj[r][k] * v[k];
+                    w[r] = s;
+                }
+                double ang = -0.5 * tau * (V ? V[j] : 0.0) / hbar;
+                cplx ph = cos(ang) + I * sin(ang);
+                for (int cc = 0; cc < 4; ++cc) psi[cc * N + j] = ph * w[cc];
+            }
+            if (half == 1) break;
+            for (int cc = 0; cc < 4; ++cc) orc_fftn(psi + cc * N, ndim, dims, -1);
+            dirac_momentum_space(psi, ndim, dims, h, mass, c, hbar, tau);
+            for (int cc = 0; cc < 4; ++cc) orc_fftn(psi + cc * N, ndim, dims, +1);
+        }
+    }
+    free(R);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* One-dimensional Dirac equation, two components (end of Sec. 2.3)    */
 /* ------------------------------------------------------------------ */

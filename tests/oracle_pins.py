@@ -464,6 +464,61 @@ def pin_dirac_energy_3d(orc):
     assert abs(orc.energy(psi, V, sp, 4) - ref) < 1e-10 * abs(ref)
 
 
+def pin_dirac_profile_uniform(orc):
+    """A vector potential that is the same in every column reproduces the
+    uniform-A step exactly."""
+    dims, sp = (12, 8), (0.05, 0.07)
+    psi0 = wl.random_state((4,) + dims[::-1], 111, sp)
+    V = wl.random_potential(dims, 112, 4.0)
+    A = wl.random_field(3, 2, 113, 30.0)
+    prof = np.repeat(A[:, None, :], dims[0], axis=1)
+    out = orc.dirac_propagate_profile(psi0, V, sp, 1e-4, 3, prof)
+    assert np.array_equal(out, orc.dirac_propagate(psi0, V, sp, 1e-4, 3, A))
+
+
+def pin_dirac_profile_shift(orc):
+    """Shifting the state, the potential and the profile A(x_1) by m columns
+    shifts the result (translation covariance of the lattice step)."""
+    dims, sp = (16, 8), (0.05, 0.06)
+    psi0 = wl.random_state((4,) + dims[::-1], 114, sp)
+    V = wl.random_potential(dims, 115, 4.0)
+    prof = 40.0 * np.random.default_rng(116).standard_normal((3, dims[0], 2))
+    m = 5
+    out = orc.dirac_propagate_profile(psi0, V, sp, 1e-4, 3, prof)
+    sh = orc.dirac_propagate_profile(np.roll(psi0, m, axis=-1), np.roll(V, m, axis=-1), sp, 1e-4, 3,
+                                     np.roll(prof, m, axis=1))
+    assert relerr(sh, np.roll(out, m, axis=-1)) < 1e-12
+
+
+def pin_dirac_profile_two_steps_numpy(orc):
+    """Two steps assembled in NumPy from the pinned pieces: the mixing of
+    Eq. 26 per column (checked against expm), the kinetic matrix of Eq. 33
+    per momentum (checked against expm), NumPy FFTs; fixes the column and
+    step indexing of the profile."""
+    dims, sp = (12, 8), (0.04, 0.05)
+    psi = wl.random_state((4,) + dims[::-1], 117, sp)
+    V = wl.random_potential(dims, 118, 3.0)
+    prof = 30.0 * np.random.default_rng(119).standard_normal((2, dims[0], 2))
+    tau = 1e-4
+    P = np.meshgrid(*[wl.momenta(m, h) for m, h in zip(dims, sp)][::-1], indexing="ij")[::-1]
+    K = {idx: orc.dirac_kinetic_matrix((P[0][idx], P[1][idx]), tau) for idx in np.ndindex(dims[1], dims[0])}
+    ph = np.exp(-0.5j * tau * V)
+    ref = psi.copy()
+    for n in range(2):
+        R = [orc.dirac_mixing_matrix(prof[n, i], tau, 0.5) for i in range(dims[0])]
+        for half in range(2):
+            for iy, ix in np.ndindex(dims[1], dims[0]):
+                ref[:, iy, ix] = ph[iy, ix] * (R[ix] @ ref[:, iy, ix])
+            if half == 1:
+                break
+            st = np.stack([np.fft.fft2(ref[k]) for k in range(4)])
+            for idx in np.ndindex(dims[1], dims[0]):
+                st[(slice(None),) + idx] = K[idx] @ st[(slice(None),) + idx]
+            ref = np.stack([np.fft.ifft2(st[k]) for k in range(4)])
+    out = orc.dirac_propagate_profile(psi, V, sp, tau, 2, prof)
+    assert relerr(out, ref) < 1e-12
+
+
 def pin_dirac_constant_potential_phase(orc):
     """A constant V0 with A = 0 only adds the global phase exp(-i V0 t) to the
     free Dirac evolution (Eqs. 21-22: the scalar factor commutes)."""
@@ -657,7 +712,8 @@ ALL_PINS = [
     pin_velocity_gauge_lattice_shift, pin_dirac1d_u_diagonalises, pin_dirac1d_free_exact,
     pin_dirac1d_constant_potential_phase, pin_dirac1d_norm_and_reversibility, pin_dirac1d_equals_2d_pair,
     pin_dirac1d_uniform_A_second_order, pin_dirac1d_energy, pin_free_dirac_exact_3d,
-    pin_dirac_uniform_A_second_order_3d, pin_dirac_energy_3d, pin_ehrenfest_field, pin_schrodinger_energy,
+    pin_dirac_uniform_A_second_order_3d, pin_dirac_energy_3d, pin_dirac_profile_uniform,
+    pin_dirac_profile_shift, pin_dirac_profile_two_steps_numpy, pin_ehrenfest_field, pin_schrodinger_energy,
     pin_dirac_algebra, pin_dirac_u_diagonalises, pin_dirac_kinetic_expm, pin_dirac_mixing_expm,
     pin_free_dirac_exact, pin_dirac_constant_potential_phase, pin_dirac_norm_and_reversibility, pin_dirac_uniform_A_second_order,
     pin_dirac_velocity, pin_dirac_energy,

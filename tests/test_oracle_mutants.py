@@ -49,6 +49,10 @@ MUTANTS = [
      [pins.pin_dirac1d_energy]),
     ("alpha3_sign", "alpha[2][0][2] = 1; alpha[2][1][3] = -1;", "alpha[2][0][2] = -1; alpha[2][1][3] = 1;",
      [pins.pin_free_dirac_exact_3d, pins.pin_dirac_uniform_A_second_order_3d]),
+    ("profile_column_index", "const cplx(*Rj)[4] = (const cplx(*)[4])R[j % nx];",
+     "const cplx(*Rj)[4] = (const cplx(*)[4])R[(j + 1) % nx];", [pins.pin_dirac_profile_two_steps_numpy]),
+    ("profile_step_index", "dirac_mixing(field + (n * nx + i) * ndim,", "dirac_mixing(field + i * ndim,",
+     [pins.pin_dirac_profile_two_steps_numpy]),
     ("lattice_origin", "return -0.5 * (double)n * h + (double)j * h;",
      "return -0.5 * (double)n * h + (double)(j + 1) * h;", [pins.pin_field_kick_plane_wave]),
     ("dirac_u_not_adjoint", "for (int k = 0; k < 4; ++k) s += conj(u[k][i]) * w[k];",
