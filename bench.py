@@ -280,6 +280,7 @@ def main():
     velocity = None
     dirac1d = None
     dirac3d = None
+    dirac_profile = None
     if args.batched and rank == 0:
         ws = wl.config5(64, n_steps=args.batch_steps)
         npts5 = sum(x.npoints for x in ws)
@@ -448,6 +449,41 @@ def main():
                    "design_frac_of_peak": design3 / (t3d / T3) / 1e9 / measured_peaks()[0]}
         q3.close()
         torch.cuda.empty_cache()
+        # 2D Dirac in a pulse travelling along x (A_y(x, t), the paper's
+        # scattering geometry) on the 1024^2 Dirac lattice, against the same
+        # plan with the uniform field of that workload
+        w4 = wl.config4(n_steps=200)
+        n4, T4 = w4.dims[0], w4.n_steps
+        x4 = wl.lattice(n4, w4.spacing[0])
+        kx = 2 * np.pi / (n4 * w4.spacing[0])
+        t4 = (np.arange(T4) + 0.5) * w4.dt
+        eta = kx * x4[None, :] - 137.036 * kx * t4[:, None]
+        A4 = np.zeros((T4, n4, 2))
+        A4[:, :, 1] = 20.0 * np.sin(eta) * np.sin(0.5 * eta) ** 2
+        qp = sop.Propagator(w4.dims, w4.spacing, 4, "c64")
+        qp.set_potential(w4.V)
+        qp.set_state(torch.from_numpy(w4.psi0))
+        qp.step(4, w4.dt, w4.field[:4])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        qp.step(T4, w4.dt, w4.field)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tu = e0.elapsed_time(e1) * 1e-3
+        qp.set_field_profile(True)
+        qp.set_state(torch.from_numpy(w4.psi0))
+        qp.step(4, w4.dt, A4[:4])
+        e0.record(stream)
+        qp.step(T4, w4.dt, A4)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tp = e0.elapsed_time(e1) * 1e-3
+        dirac_profile = {"value": n4 * n4 * T4 / tp, "unit": UNIT, "dtype": "f32",
+                         "workload": f"2D Dirac {n4}^2 (config-4 lattice and potential), A_y(x, t) of a pulse "
+                                     f"travelling along x, {T4} steps, per-column mixing as its own pass",
+                         "us_per_step": tp / T4 * 1e6, "uniform_A_us_per_step": tu / T4 * 1e6}
+        qp.close()
+        torch.cuda.empty_cache()
 
     # ---- FP64 sample, same lattice -----------------------------------------
     fp64 = None
@@ -542,7 +578,7 @@ def main():
                              "within a step",
                        "parallelism": f"replicas x{world} (independent problems, no data-path collective)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "fp64": fp64, "batched": batched, "adjoint": adjoint, "spectral": spectral, "velocity_gauge": velocity, "dirac1d": dirac1d, "dirac3d": dirac3d, "err_vs_oracle": err, "clocks": clocks,
+            "fp64": fp64, "batched": batched, "adjoint": adjoint, "spectral": spectral, "velocity_gauge": velocity, "dirac1d": dirac1d, "dirac3d": dirac3d, "dirac_profile": dirac_profile, "err_vs_oracle": err, "clocks": clocks,
         }
         s = json.dumps(line)
         print(s, flush=True)

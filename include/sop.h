@@ -119,6 +119,17 @@ int sop_set_potential(sop_plan plan, const void *V_dev, int v_is_fp64);
  * device for every 512 steps).  Dirac plans always take A (SOP_EUNSUPPORTED
  * here).  The adjoint gradient and batches accept length-gauge plans only.
  * Returns SOP_EINVAL for another value. */
+/* Dirac plans (components = 4, 2D or 3D): along_x1 = 1 makes the field
+ * samples a vector potential that varies along x_1, A(x_1, t), as for a
+ * plane-wave laser pulse travelling along x_1 (the paper's scattering
+ * example): field_samples then holds n_steps x dims[0] x ndim doubles, A at
+ * each step's midpoint and lattice column i of axis 0 ([step][i][component]).
+ * The mixing of Eq. 26 is then formed per column (on the device, in FP64, for
+ * every 64 steps) and applied as a streaming pass of its own between the x
+ * transforms; along_x1 = 0 (the default) is the uniform A.  Returns
+ * SOP_EUNSUPPORTED for other plans, SOP_EINVAL for another value. */
+int sop_set_field_profile(sop_plan plan, int along_x1);
+
 #define SOP_GAUGE_LENGTH 0
 #define SOP_GAUGE_VELOCITY 1
 int sop_set_gauge(sop_plan plan, int gauge);

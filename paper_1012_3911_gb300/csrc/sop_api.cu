@@ -48,6 +48,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr int64_t kFieldChunk = 512;   // real-space indices per field-table chunk
+constexpr int64_t kProfileChunk = 64;  // real-space indices per chunk of per-column mixing matrices
 constexpr int kStageSlots = 8;         // pinned upload slots in flight
 
 struct EventPair {
@@ -79,8 +80,9 @@ struct sop_plan_s {
     void *vhalf = nullptr, *vfull = nullptr;
     void *kin[3] = {nullptr, nullptr, nullptr};
     void *dtab = nullptr;
-    void *mtab = nullptr;           // 1D Dirac: merged mixing rows of one call
-    size_t mtab_cap = 0;
+    void *mtab = nullptr;           // 1D Dirac: merged mixing rows of one call; Dirac with a
+    size_t mtab_cap = 0;            // column-dependent A: kProfileChunk rows of per-column matrices
+    bool profile = false;           // Dirac: field samples per lattice column of axis 0
     double *theta = nullptr;        // device scratch for per-axis angles
     double tables_dt = std::nan("");
     bool tables_valid = false;
@@ -552,8 +554,9 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
     if (n < 0) return fail(SOP_EINVAL, "sop_step: n_steps < 0");
     if (!is_finite(dt)) return fail(SOP_EINVAL, "sop_step: dt is not finite");
     if (n == 0) return SOP_OK;
+    const int64_t per_step = (int64_t)p->ndim * (p->profile ? p->dims[0] : 1);   // samples per step
     if (field)
-        for (int64_t i = 0; i < n * p->ndim; ++i)
+        for (int64_t i = 0; i < n * per_step; ++i)
             if (!is_finite(field[i])) return fail(SOP_EINVAL, "sop_step: field sample is not finite");
     int rc = ensure_tables(p, dt);
     if (rc) return rc;
@@ -563,6 +566,89 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
     auto sample = [&](int64_t s, int a) -> double {
         return (field && s >= 0 && s < n) ? field[s * nd + a] : 0.0;
     };
+    // Dirac with a column-dependent vector potential: the samples go to the
+    // device once per call, the merged mixing matrices per chunk of steps.
+    const bool prof = p->comps == 4 && p->profile && field;
+    const int64_t nx = p->dims[0];
+    if (prof) {
+        const int64_t cnt = n * per_step;
+        if (p->fvec_cap < cnt) {
+            cudaStreamSynchronize(p->stream);
+            dfree(p->fvec);
+            p->fvec = nullptr;
+            p->fvec_cap = 0;
+            rc = dalloc(&p->fvec, (size_t)cnt * sizeof(double), "field samples");
+            if (rc) return rc;
+            p->fvec_cap = cnt;
+        }
+        rc = upload(p, p->fvec, field, cnt);
+        if (rc) return rc;
+        const size_t need = (size_t)kProfileChunk * nx * 16 * p->csz;
+        if (p->mtab_cap < need) {
+            cudaStreamSynchronize(p->stream);
+            dfree(p->mtab);
+            p->mtab = nullptr;
+            p->mtab_cap = 0;
+            rc = dalloc(&p->mtab, need, "mixing matrices");
+            if (rc) return rc;
+            p->mtab_cap = need;
+        }
+    }
+    auto mix_rows = [&](int64_t P0, int64_t P1) -> int {   // rows P0 .. P1-1 into p->mtab
+        Bracket br(p, 4);
+        cudaError_t e = build_mix_rows(p->mtab, p->fvec, P0, P1 - P0, nx, nd, n, p->prm.charge, p->prm.c, hbar, dt,
+                                       p->f64, p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "mixing matrices");
+        br.done();
+        return SOP_OK;
+    };
+    auto mix_row = [&](int64_t P, int64_t P0) -> const void * {
+        return static_cast<const char *>(p->mtab) + (size_t)(P - P0) * nx * 16 * p->csz;
+    };
+
+    if (prof && nd == 2) {
+        // ---- Dirac, 2D, column-dependent A: the mixing runs as its own
+        // streaming pass between the x transforms of the four components;
+        // the momentum-space factor stays fused in the y pass of the pairs.
+        for (int64_t P0 = 0; P0 <= n; P0 += kProfileChunk) {
+            const int64_t P1 = std::min<int64_t>(n + 1, P0 + kProfileChunk);
+            if ((rc = mix_rows(P0, P1))) return rc;
+            for (int64_t P = P0; P < P1; ++P) {
+                const bool smp = step_sampled(p, P);
+                if (P > 0) {
+                    PassArgs a;
+                    base_args(p, a, p->psi, 0);
+                    a.n_batch = 4;
+                    a.pre = +1;
+                    a.op = OP_NONE;
+                    if ((rc = run_pass(p, a, 1, 2, "Dirac inverse x transform", smp))) return rc;
+                }
+                {
+                    Bracket br(p, 0, smp);
+                    cudaError_t e = launch_dirac3_real(p->psi, p->npts,
+                                                       p->v_set ? ((P == 0 || P == n) ? p->vhalf : p->vfull) : nullptr,
+                                                       nullptr, mix_row(P, P0), nx, p->f64, p->stream);
+                    if (e != cudaSuccess) return cuda_fail(e, "Dirac real-space factor");
+                    br.done();
+                }
+                if (P == n) break;
+                PassArgs a;
+                base_args(p, a, p->psi, 0);
+                a.n_batch = 4;
+                a.pre = -1;
+                a.op = OP_NONE;
+                if ((rc = run_pass(p, a, 1, 2, "Dirac forward x transform", smp))) return rc;
+                PassArgs k;
+                base_args(p, k, p->psi, 1);
+                k.pre = -1;
+                k.post = +1;
+                k.op = OP_DT;
+                k.dtab = p->dtab;
+                if ((rc = run_pass(p, k, 2, 1, "Dirac momentum-space pass", smp))) return rc;
+            }
+        }
+        return SOP_OK;
+    }
 
     if (p->comps == 2) {
         // ---- Dirac, 1D, two components: whole steps on chip ----------------
@@ -650,7 +736,7 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
         auto R = [&](int64_t s, cd M[4][4]) {
             double Ab[3] = {0, 0, 0}, mag = 0.0;
             for (int a = 0; a < 3; ++a) {
-                Ab[a] = sample(s, a) * dt;
+                Ab[a] = prof ? 0.0 : sample(s, a) * dt;   // (per-column matrices come from mix_rows)
                 mag += Ab[a] * Ab[a];
             }
             mag = std::sqrt(mag);
@@ -663,7 +749,12 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
                     M[i][j] = v;
                 }
         };
+        int64_t P0 = 0;
         for (int64_t P = 0; P <= n; ++P) {
+            if (prof && (P - P0 == kProfileChunk || P == 0)) {
+                P0 = P;
+                if ((rc = mix_rows(P0, std::min<int64_t>(n + 1, P0 + kProfileChunk)))) return rc;
+            }
             cd Rn[4][4], Rp[4][4];
             R(P, Rn);
             R(P - 1, Rp);
@@ -680,7 +771,8 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
                 Bracket br(p, 0, smp);
                 cudaError_t e = launch_dirac3_real(p->psi, p->npts, p->v_set ? ((P == 0 || P == n) ? p->vhalf : p->vfull)
                                                                              : nullptr,
-                                                   Md, p->f64, p->stream);
+                                                   prof ? nullptr : Md, prof ? mix_row(P, P0) : nullptr, nx, p->f64,
+                                                   p->stream);
                 if (e != cudaSuccess) return cuda_fail(e, "3D Dirac real-space factor");
                 br.done();
             }
@@ -1047,6 +1139,14 @@ int sop_set_potential(sop_plan p, const void *V_dev, int v_is_fp64) {
     br.done();
     p->v_set = true;
     p->tables_valid = false;
+    return SOP_OK;
+}
+
+int sop_set_field_profile(sop_plan p, int along_x1) {
+    if (!p) return fail(SOP_EINVAL, "sop_set_field_profile: null plan");
+    if (p->comps != 4) return fail(SOP_EUNSUPPORTED, "sop_set_field_profile: four-component Dirac plans only");
+    if (along_x1 != 0 && along_x1 != 1) return fail(SOP_EINVAL, "sop_set_field_profile: along_x1 must be 0 or 1");
+    p->profile = along_x1 == 1;
     return SOP_OK;
 }
 

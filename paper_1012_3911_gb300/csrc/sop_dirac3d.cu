@@ -7,7 +7,9 @@
 // separate pencil passes (components as a batch) and applies the two 4x4
 // factors here, one streaming pass over the four components each:
 //   real space:      psi <- exp(-i V tau') M psi, M the merged mixing of the
-//                    adjacent half steps (Eqs. 21-26), uniform in space;
+//                    adjacent half steps (Eqs. 21-26), uniform in space or,
+//                    for a vector potential that varies along x_1, one 4x4
+//                    matrix per lattice column (k_mix_rows builds them);
 //   momentum space:  psi~ <- (1/N) [cos(E tau) - i sin(E tau) H(p)/E] psi~,
 //                    H = c alpha.p + m c^2 beta (the closed form of Eq. 33).
 #include "sop_kernels.cuh"
@@ -56,9 +58,12 @@ template <typename Real> struct Mix4 {
     cplx_t<Real> m[16];   // row-major 4x4
 };
 
+// psi <- exp(-i V tau') M psi on all points; M uniform (by value) or, with
+// rows != null, the 4x4 matrix of the point's column x_1 (rows[(j mod nx) 16 ...],
+// a vector potential that varies along x_1).
 template <typename Real>
 __global__ void __launch_bounds__(kThreads) k_dirac3_real(cplx_t<Real> *psi, int64_t npts, const cplx_t<Real> *vtab,
-                                                          Mix4<Real> M) {
+                                                          Mix4<Real> M, const cplx_t<Real> *rows, int64_t nx) {
     using C = cplx_t<Real>;
     using Ph = Phase<Real>;
     for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < npts; j += (int64_t)gridDim.x * kThreads) {
@@ -66,14 +71,72 @@ __global__ void __launch_bounds__(kThreads) k_dirac3_real(cplx_t<Real> *psi, int
 #pragma unroll
         for (int c = 0; c < 4; ++c) v[c] = __ldcg(psi + c * npts + j);
         const C f = vtab ? __ldcg(vtab + j) : Ph::one();
+        const C *mr = rows ? rows + (j % nx) * 16 : nullptr;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            C w = cmul(M.m[4 * i], v[0]);
+            C m[4];
 #pragma unroll
-            for (int k = 1; k < 4; ++k) w = cadd(w, cmul(M.m[4 * i + k], v[k]));
+            for (int k = 0; k < 4; ++k) m[k] = mr ? __ldg(mr + 4 * i + k) : M.m[4 * i + k];
+            C w = cmul(m[0], v[0]);
+#pragma unroll
+            for (int k = 1; k < 4; ++k) w = cadd(w, cmul(m[k], v[k]));
             if (vtab) w = Ph::apply(w, f);
             __stcg(psi + i * npts + j, w);
         }
+    }
+}
+
+// Half-step mixing of Eq. 26 for a vector potential Abar = A tau (ndim
+// components), delta = 1/2: R = cos th + i sin th sum_a (Abar_a/Abar) alpha_a,
+// th = q c Abar / (2 hbar); alpha in the Dirac representation.
+__device__ void mixing4(const double *A, int ndim, double qc2h, double tau, double2 R[16]) {
+    double Ab[3] = {0, 0, 0}, mag = 0.0;
+    for (int a = 0; a < ndim; ++a) {
+        Ab[a] = A ? A[a] * tau : 0.0;
+        mag += Ab[a] * Ab[a];
+    }
+    mag = sqrt(mag);
+    double s, co;
+    sincos(qc2h * mag, &s, &co);
+    const double nx = mag > 0 ? Ab[0] / mag : 0.0, ny = mag > 0 ? Ab[1] / mag : 0.0, nz = mag > 0 ? Ab[2] / mag : 0.0;
+    for (int q = 0; q < 16; ++q) R[q] = make_double2(q % 5 == 0 ? co : 0.0, 0.0);
+    // i s (n.alpha): alpha_1 (0,3)(1,2)(2,1)(3,0) = 1; alpha_2 (0,3) = -i, (1,2) = i,
+    // (2,1) = -i, (3,0) = i; alpha_3 (0,2) = 1, (1,3) = -1, (2,0) = 1, (3,1) = -1
+    // entries of sum n_a alpha_a: (0,3) = nx - i ny, (1,2) = nx + i ny, (2,1) = nx - i ny,
+    // (3,0) = nx + i ny, (0,2) = nz, (1,3) = -nz, (2,0) = nz, (3,1) = -nz; times i s.
+    auto put = [&](int r, int c, double re, double im) { R[4 * r + c] = make_double2(-s * im, s * re); };
+    put(0, 3, nx, -ny);
+    put(1, 2, nx, ny);
+    put(2, 1, nx, -ny);
+    put(3, 0, nx, ny);
+    put(0, 2, nz, 0.0);
+    put(1, 3, -nz, 0.0);
+    put(2, 0, nz, 0.0);
+    put(3, 1, -nz, 0.0);
+}
+
+// Rows P0 .. P0 + n_rows - 1 of merged mixing matrices per column:
+// out[(P - P0) nx + i] = R(A_P(i)) R(A_{P-1}(i)), with A_s(i) =
+// avec[(s nx + i) ndim ...] for 0 <= s < n_steps and 0 (identity) otherwise.
+__global__ void k_mix_rows(void *out, const double *avec, int64_t P0, int64_t n_rows, int64_t nx, int ndim,
+                           int64_t n_steps, double qc2h, double tau, bool f64) {
+    const int64_t total = n_rows * nx;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t P = P0 + e / nx, i = e % nx;
+        double2 Rn[16], Rp[16];
+        mixing4(P < n_steps ? avec + (P * nx + i) * ndim : nullptr, ndim, qc2h, tau, Rn);
+        mixing4(P > 0 ? avec + ((P - 1) * nx + i) * ndim : nullptr, ndim, qc2h, tau, Rp);
+        for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) {
+                double re = 0.0, im = 0.0;
+                for (int k = 0; k < 4; ++k) {
+                    const double2 a = Rn[4 * r + k], b = Rp[4 * k + c];
+                    re += a.x * b.x - a.y * b.y;
+                    im += a.x * b.y + a.y * b.x;
+                }
+                if (f64) reinterpret_cast<double2 *>(out)[e * 16 + 4 * r + c] = make_double2(re, im);
+                else reinterpret_cast<float2 *>(out)[e * 16 + 4 * r + c] = make_float2((float)re, (float)im);
+            }
     }
 }
 
@@ -114,14 +177,17 @@ __global__ void __launch_bounds__(kThreads) k_dirac3_kinetic(cplx_t<Real> *psi, 
 }
 
 template <typename Real>
-cudaError_t dirac3_real_t(void *psi, int64_t npts, const void *vtab, const double *Md, cudaStream_t s) {
-    Mix4<Real> M;   // (host code: no device helpers)
-    for (int q = 0; q < 16; ++q) {
-        M.m[q].x = (Real)Md[2 * q];
-        M.m[q].y = (Real)Md[2 * q + 1];
-    }
+cudaError_t dirac3_real_t(void *psi, int64_t npts, const void *vtab, const double *Md, const void *rows, int64_t nx,
+                          cudaStream_t s) {
+    Mix4<Real> M{};   // (host code: no device helpers)
+    if (Md)
+        for (int q = 0; q < 16; ++q) {
+            M.m[q].x = (Real)Md[2 * q];
+            M.m[q].y = (Real)Md[2 * q + 1];
+        }
     k_dirac3_real<Real><<<kBlocks, kThreads, 0, s>>>(static_cast<cplx_t<Real> *>(psi), npts,
-                                                      static_cast<const cplx_t<Real> *>(vtab), M);
+                                                      static_cast<const cplx_t<Real> *>(vtab), M,
+                                                      static_cast<const cplx_t<Real> *>(rows), nx);
     return cudaGetLastError();
 }
 
@@ -134,9 +200,19 @@ cudaError_t build_dirac3_table(void *out, const int64_t *dims, const double *h, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_dirac3_real(void *psi, int64_t npts, const void *vtab, const double *M, bool f64,
-                               cudaStream_t s) {
-    return f64 ? dirac3_real_t<double>(psi, npts, vtab, M, s) : dirac3_real_t<float>(psi, npts, vtab, M, s);
+cudaError_t launch_dirac3_real(void *psi, int64_t npts, const void *vtab, const double *M, const void *rows,
+                               int64_t nx, bool f64, cudaStream_t s) {
+    return f64 ? dirac3_real_t<double>(psi, npts, vtab, M, rows, nx, s)
+               : dirac3_real_t<float>(psi, npts, vtab, M, rows, nx, s);
+}
+
+cudaError_t build_mix_rows(void *out, const double *avec, int64_t P0, int64_t n_rows, int64_t nx, int ndim,
+                           int64_t n_steps, double charge, double c, double hbar, double tau, bool f64,
+                           cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    k_mix_rows<<<kBlocks, kThreads, 0, s>>>(out, avec, P0, n_rows, nx, ndim, n_steps, 0.5 * charge * c / hbar, tau,
+                                            f64);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dirac3_kinetic(void *psi, int64_t npts, const void *tab, double shi, double slo, bool f64,

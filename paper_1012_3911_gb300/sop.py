@@ -254,6 +254,14 @@ def sop_set_gauge(plan: int, gauge: int) -> None:
     _check(lib.sop_set_gauge(plan, int(gauge)))
 
 
+def sop_set_field_profile(plan: int, along_x1: bool) -> None:
+    """Dirac plans: field samples per lattice column of axis 0, A(x_1, t)."""
+    lib = load()
+    lib.sop_set_field_profile.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.sop_set_field_profile.restype = ctypes.c_int
+    _check(lib.sop_set_field_profile(plan, 1 if along_x1 else 0))
+
+
 SOP_SPECTRAL_MAX_EIGEN = 16
 
 
@@ -387,8 +395,14 @@ class Propagator:
             raise ValueError("gauge must be 'length' or 'velocity'")
         sop_set_gauge(self.plan, SOP_GAUGE_LENGTH if gauge == "length" else SOP_GAUGE_VELOCITY)
 
+    def set_field_profile(self, along_x1: bool) -> None:
+        """Dirac: field samples of shape (n_steps, n_x, ndim), A per column of x_1."""
+        sop_set_field_profile(self.plan, along_x1)
+        self.profile = bool(along_x1)
+
     def step(self, n_steps: int, dt: float, field=None) -> None:
-        sop_step(self.plan, n_steps, dt, field, self.ndim)
+        row = self.ndim * (self.dims[0] if getattr(self, "profile", False) else 1)
+        sop_step(self.plan, n_steps, dt, field, row)
 
     def step_host(self, psi_host, n_steps: int, dt: float, field=None) -> None:
         sop_step_host(self.plan, psi_host, n_steps, dt, field, self.ndim)
