@@ -583,7 +583,7 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
         }
         rc = upload(p, p->fvec, field, cnt);
         if (rc) return rc;
-        const size_t need = (size_t)kProfileChunk * nx * 16 * p->csz;
+        const size_t need = (size_t)kProfileChunk * nx * 4 * p->csz;   // 8 reals per column
         if (p->mtab_cap < need) {
             cudaStreamSynchronize(p->stream);
             dfree(p->mtab);
@@ -603,7 +603,7 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
         return SOP_OK;
     };
     auto mix_row = [&](int64_t P, int64_t P0) -> const void * {
-        return static_cast<const char *>(p->mtab) + (size_t)(P - P0) * nx * 16 * p->csz;
+        return static_cast<const char *>(p->mtab) + (size_t)(P - P0) * nx * 4 * p->csz;
     };
 
     if (prof && nd == 2) {

@@ -8,8 +8,8 @@
 // factors here, one streaming pass over the four components each:
 //   real space:      psi <- exp(-i V tau') M psi, M the merged mixing of the
 //                    adjacent half steps (Eqs. 21-26), uniform in space or,
-//                    for a vector potential that varies along x_1, one 4x4
-//                    matrix per lattice column (k_mix_rows builds them);
+//                    for a vector potential that varies along x_1, one
+//                    compact matrix per lattice column (k_mix_rows);
 //   momentum space:  psi~ <- (1/N) [cos(E tau) - i sin(E tau) H(p)/E] psi~,
 //                    H = c alpha.p + m c^2 beta (the closed form of Eq. 33).
 #include "sop_kernels.cuh"
@@ -58,12 +58,14 @@ template <typename Real> struct Mix4 {
     cplx_t<Real> m[16];   // row-major 4x4
 };
 
-// psi <- exp(-i V tau') M psi on all points; M uniform (by value) or, with
-// rows != null, the 4x4 matrix of the point's column x_1 (rows[(j mod nx) 16 ...],
-// a vector potential that varies along x_1).
+// psi <- exp(-i V tau') M psi on all points; M uniform (by value, a general
+// 4x4) or, with rows != null, the merged mixing of the point's column x_1 in
+// the compact form M = a + i b.alpha + i d.Sigma (8 reals per column:
+// a, b_1..3, d_1..3, 0; Sigma_k = diag(sigma_k, sigma_k)), for a vector
+// potential that varies along x_1.
 template <typename Real>
 __global__ void __launch_bounds__(kThreads) k_dirac3_real(cplx_t<Real> *psi, int64_t npts, const cplx_t<Real> *vtab,
-                                                          Mix4<Real> M, const cplx_t<Real> *rows, int64_t nx) {
+                                                          Mix4<Real> M, const Real *rows, int64_t nx) {
     using C = cplx_t<Real>;
     using Ph = Phase<Real>;
     for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < npts; j += (int64_t)gridDim.x * kThreads) {
@@ -71,72 +73,85 @@ __global__ void __launch_bounds__(kThreads) k_dirac3_real(cplx_t<Real> *psi, int
 #pragma unroll
         for (int c = 0; c < 4; ++c) v[c] = __ldcg(psi + c * npts + j);
         const C f = vtab ? __ldcg(vtab + j) : Ph::one();
-        const C *mr = rows ? rows + (j % nx) * 16 : nullptr;
+        C w[4];
+        if (rows) {
+            Real q[8];
+            const Real *r = rows + (j % nx) * 8;
+            if constexpr (sizeof(Real) == 4) {
+                const float4 x0 = __ldg(reinterpret_cast<const float4 *>(r)), x1 = __ldg(reinterpret_cast<const float4 *>(r) + 1);
+                q[0] = x0.x; q[1] = x0.y; q[2] = x0.z; q[3] = x0.w; q[4] = x1.x; q[5] = x1.y; q[6] = x1.z; q[7] = x1.w;
+            } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            C m[4];
+                for (int k = 0; k < 4; ++k) {
+                    const double2 x = __ldg(reinterpret_cast<const double2 *>(r) + k);
+                    q[2 * k] = x.x;
+                    q[2 * k + 1] = x.y;
+                }
+            }
+            const Real a = q[0], b1 = q[1], b2 = q[2], b3 = q[3], d1 = q[4], d2 = q[5], d3 = q[6];
+            const C bm = mk<C>(b1, -b2), bp = mk<C>(b1, b2), dm = mk<C>(d1, -d2), dp = mk<C>(d1, d2);
+            // (b.alpha v) and (d.Sigma v), then w = a v + i (b.alpha v + d.Sigma v)
+            C u[4];
+            u[0] = cadd(cadd(cmul(bm, v[3]), cscale(v[2], b3)), cadd(cscale(v[0], d3), cmul(dm, v[1])));
+            u[1] = cadd(csub(cmul(bp, v[2]), cscale(v[3], b3)), csub(cmul(dp, v[0]), cscale(v[1], d3)));
+            u[2] = cadd(cadd(cmul(bm, v[1]), cscale(v[0], b3)), cadd(cscale(v[2], d3), cmul(dm, v[3])));
+            u[3] = cadd(csub(cmul(bp, v[0]), cscale(v[1], b3)), csub(cmul(dp, v[2]), cscale(v[3], d3)));
 #pragma unroll
-            for (int k = 0; k < 4; ++k) m[k] = mr ? __ldg(mr + 4 * i + k) : M.m[4 * i + k];
-            C w = cmul(m[0], v[0]);
+            for (int c = 0; c < 4; ++c) w[c] = cadd(cscale(v[c], a), mul_pi(u[c]));
+        } else {
 #pragma unroll
-            for (int k = 1; k < 4; ++k) w = cadd(w, cmul(m[k], v[k]));
-            if (vtab) w = Ph::apply(w, f);
-            __stcg(psi + i * npts + j, w);
+            for (int i = 0; i < 4; ++i) {
+                C acc = cmul(M.m[4 * i], v[0]);
+#pragma unroll
+                for (int k = 1; k < 4; ++k) acc = cadd(acc, cmul(M.m[4 * i + k], v[k]));
+                w[i] = acc;
+            }
         }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) __stcg(psi + c * npts + j, vtab ? Ph::apply(w[c], f) : w[c]);
     }
 }
 
 // Half-step mixing of Eq. 26 for a vector potential Abar = A tau (ndim
-// components), delta = 1/2: R = cos th + i sin th sum_a (Abar_a/Abar) alpha_a,
-// th = q c Abar / (2 hbar); alpha in the Dirac representation.
-__device__ void mixing4(const double *A, int ndim, double qc2h, double tau, double2 R[16]) {
+// components), delta = 1/2: R = cos th + i sin th n.alpha with n = Abar/|Abar|
+// and th = q c |Abar| / (2 hbar).
+__device__ void mixing_params(const double *A, int ndim, double qc2h, double tau, double &c, double &s, double n[3]) {
     double Ab[3] = {0, 0, 0}, mag = 0.0;
     for (int a = 0; a < ndim; ++a) {
         Ab[a] = A ? A[a] * tau : 0.0;
         mag += Ab[a] * Ab[a];
     }
     mag = sqrt(mag);
-    double s, co;
-    sincos(qc2h * mag, &s, &co);
-    const double nx = mag > 0 ? Ab[0] / mag : 0.0, ny = mag > 0 ? Ab[1] / mag : 0.0, nz = mag > 0 ? Ab[2] / mag : 0.0;
-    for (int q = 0; q < 16; ++q) R[q] = make_double2(q % 5 == 0 ? co : 0.0, 0.0);
-    // i s (n.alpha): alpha_1 (0,3)(1,2)(2,1)(3,0) = 1; alpha_2 (0,3) = -i, (1,2) = i,
-    // (2,1) = -i, (3,0) = i; alpha_3 (0,2) = 1, (1,3) = -1, (2,0) = 1, (3,1) = -1
-    // entries of sum n_a alpha_a: (0,3) = nx - i ny, (1,2) = nx + i ny, (2,1) = nx - i ny,
-    // (3,0) = nx + i ny, (0,2) = nz, (1,3) = -nz, (2,0) = nz, (3,1) = -nz; times i s.
-    auto put = [&](int r, int c, double re, double im) { R[4 * r + c] = make_double2(-s * im, s * re); };
-    put(0, 3, nx, -ny);
-    put(1, 2, nx, ny);
-    put(2, 1, nx, -ny);
-    put(3, 0, nx, ny);
-    put(0, 2, nz, 0.0);
-    put(1, 3, -nz, 0.0);
-    put(2, 0, nz, 0.0);
-    put(3, 1, -nz, 0.0);
+    sincos(qc2h * mag, &s, &c);
+    for (int a = 0; a < 3; ++a) n[a] = mag > 0 ? Ab[a] / mag : 0.0;
 }
 
-// Rows P0 .. P0 + n_rows - 1 of merged mixing matrices per column:
-// out[(P - P0) nx + i] = R(A_P(i)) R(A_{P-1}(i)), with A_s(i) =
+// Rows P0 .. P0 + n_rows - 1 of the merged mixing per column,
+// R(A_P(i)) R(A_{P-1}(i)) = a + i b.alpha + i d.Sigma with
+// (alpha_j alpha_k = delta_jk + i eps_jkl Sigma_l)
+//   a = c_n c_p - s_n s_p n_n.n_p,  b = c_n s_p n_p + s_n c_p n_n,
+//   d = -s_n s_p n_n x n_p,
+// stored as 8 reals (a, b, d, 0) per column in the plan's precision; A_s(i) =
 // avec[(s nx + i) ndim ...] for 0 <= s < n_steps and 0 (identity) otherwise.
 __global__ void k_mix_rows(void *out, const double *avec, int64_t P0, int64_t n_rows, int64_t nx, int ndim,
                            int64_t n_steps, double qc2h, double tau, bool f64) {
     const int64_t total = n_rows * nx;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t P = P0 + e / nx, i = e % nx;
-        double2 Rn[16], Rp[16];
-        mixing4(P < n_steps ? avec + (P * nx + i) * ndim : nullptr, ndim, qc2h, tau, Rn);
-        mixing4(P > 0 ? avec + ((P - 1) * nx + i) * ndim : nullptr, ndim, qc2h, tau, Rp);
-        for (int r = 0; r < 4; ++r)
-            for (int c = 0; c < 4; ++c) {
-                double re = 0.0, im = 0.0;
-                for (int k = 0; k < 4; ++k) {
-                    const double2 a = Rn[4 * r + k], b = Rp[4 * k + c];
-                    re += a.x * b.x - a.y * b.y;
-                    im += a.x * b.y + a.y * b.x;
-                }
-                if (f64) reinterpret_cast<double2 *>(out)[e * 16 + 4 * r + c] = make_double2(re, im);
-                else reinterpret_cast<float2 *>(out)[e * 16 + 4 * r + c] = make_float2((float)re, (float)im);
-            }
+        double cn, sn, nn[3], cp, sp, np[3];
+        mixing_params(P < n_steps ? avec + (P * nx + i) * ndim : nullptr, ndim, qc2h, tau, cn, sn, nn);
+        mixing_params(P > 0 ? avec + ((P - 1) * nx + i) * ndim : nullptr, ndim, qc2h, tau, cp, sp, np);
+        double q[8];
+        q[0] = cn * cp - sn * sp * (nn[0] * np[0] + nn[1] * np[1] + nn[2] * np[2]);
+        for (int k = 0; k < 3; ++k) q[1 + k] = cn * sp * np[k] + sn * cp * nn[k];
+        q[4] = -sn * sp * (nn[1] * np[2] - nn[2] * np[1]);
+        q[5] = -sn * sp * (nn[2] * np[0] - nn[0] * np[2]);
+        q[6] = -sn * sp * (nn[0] * np[1] - nn[1] * np[0]);
+        q[7] = 0.0;
+        for (int k = 0; k < 8; ++k) {
+            if (f64) reinterpret_cast<double *>(out)[e * 8 + k] = q[k];
+            else reinterpret_cast<float *>(out)[e * 8 + k] = (float)q[k];
+        }
     }
 }
 
@@ -187,7 +202,7 @@ cudaError_t dirac3_real_t(void *psi, int64_t npts, const void *vtab, const doubl
         }
     k_dirac3_real<Real><<<kBlocks, kThreads, 0, s>>>(static_cast<cplx_t<Real> *>(psi), npts,
                                                       static_cast<const cplx_t<Real> *>(vtab), M,
-                                                      static_cast<const cplx_t<Real> *>(rows), nx);
+                                                      static_cast<const Real *>(rows), nx);
     return cudaGetLastError();
 }
 

@@ -118,10 +118,10 @@ cudaError_t build_dirac3_table(void *out, const int64_t *dims, const double *h, 
                                double dt, bool f64, cudaStream_t s);
 cudaError_t launch_dirac3_real(void *psi, int64_t npts, const void *vtab, const double *M, const void *rows,
                                int64_t nx, bool f64, cudaStream_t s);
-// Merged mixing matrices per column for rows P0 .. P0 + n_rows - 1 (16 complex
-// of the plan's precision each, [row][column][16]) from the device samples
-// avec (n_steps x nx x ndim doubles); rows M = null in launch_dirac3_real
-// uses them instead of the uniform M.
+// Merged mixing per column for rows P0 .. P0 + n_rows - 1 (8 reals of the
+// plan's precision each, [row][column][8]: a, b, d, 0 of a + i b.alpha +
+// i d.Sigma) from the device samples avec (n_steps x nx x ndim doubles);
+// with M = null, launch_dirac3_real uses these rows instead of the uniform M.
 cudaError_t build_mix_rows(void *out, const double *avec, int64_t P0, int64_t n_rows, int64_t nx, int ndim,
                            int64_t n_steps, double charge, double c, double hbar, double tau, bool f64,
                            cudaStream_t s);
