@@ -80,15 +80,30 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+# The sources the pencil-pass kernels are compiled from (device code and the
+# argument structures); host-side driver files do not change them.
+PASS_KERNEL_FILES = ("sop_async.cuh", "sop_fft.cuh", "sop_kernels.cuh", "sop_internal.h", "sop_pass_inst.cu")
+
+
+def pass_kernel_hash() -> str:
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_1012_3911_gb300", "csrc")
+    for name in PASS_KERNEL_FILES:
+        with open(os.path.join(cs, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic(kernel_class: str):
     """Per-launch DRAM bytes of a pass class from the committed ncu summary,
-    or None when the kernels changed since it was captured."""
+    or None when the pass kernels' sources changed since it was captured."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
-    if d.get("kernel_source_hash") != kernel_source_hash():
+    if d.get("pass_kernel_hash") != pass_kernel_hash():
         return None
     ent = d.get("per_launch_dram_bytes", {}).get(kernel_class)
     return None if ent is None else float(ent)
@@ -260,6 +275,7 @@ def main():
                 "traffic": ncu_traffic(names[dom]), "kernel": names[dom], "peak_source": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
                 "profile_every": args.profile_every,
+                "source_hash": kernel_source_hash(), "pass_kernel_hash": pass_kernel_hash(),
                 "pass_avg_ms": {names[i]: cls_ms[i] / cls_n[i] for i in range(len(cls_ms)) if cls_n[i]},
                 "pass_timed_launches": {names[i]: cls_n[i] for i in range(len(cls_ms)) if cls_n[i]}}
     # whole split step against the byte model: B_min = two psi round trips + FP32 V;
