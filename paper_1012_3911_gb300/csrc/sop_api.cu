@@ -548,306 +548,317 @@ int prepare_fields(sop_plan p, int64_t n, double dt, const double *field, FieldR
     return SOP_OK;
 }
 
-int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
-    if (!p) return fail(SOP_EINVAL, "sop_step: null plan");
-    if (!p->psi) return fail(SOP_ESTATE, "sop_step: no state bound (call sop_bind_state first)");
-    if (n < 0) return fail(SOP_EINVAL, "sop_step: n_steps < 0");
-    if (!is_finite(dt)) return fail(SOP_EINVAL, "sop_step: dt is not finite");
-    if (n == 0) return SOP_OK;
-    const int64_t per_step = (int64_t)p->ndim * (p->profile ? p->dims[0] : 1);   // samples per step
-    if (field)
-        for (int64_t i = 0; i < n * per_step; ++i)
-            if (!is_finite(field[i])) return fail(SOP_EINVAL, "sop_step: field sample is not finite");
-    int rc = ensure_tables(p, dt);
-    if (rc) return rc;
+// Field sample a of step s of a call of n steps (0 outside the call or
+// without a field).
+double field_sample(const double *field, int64_t n, int nd, int64_t s, int a) {
+    return (field && s >= 0 && s < n) ? field[s * nd + a] : 0.0;
+}
 
+// Dirac with a vector potential that varies along x_1: the call's samples
+// (n x dims[0] x ndim) go to the device once, and room for kProfileChunk rows
+// of per-column mixing is reserved.
+int prepare_profile(sop_plan p, int64_t n, const double *field) {
+    const int64_t nx = p->dims[0];
+    const int64_t cnt = n * nx * p->ndim;
+    int rc = SOP_OK;
+    if (p->fvec_cap < cnt) {
+        cudaStreamSynchronize(p->stream);
+        dfree(p->fvec);
+        p->fvec = nullptr;
+        p->fvec_cap = 0;
+        rc = dalloc(&p->fvec, (size_t)cnt * sizeof(double), "field samples");
+        if (rc) return rc;
+        p->fvec_cap = cnt;
+    }
+    rc = upload(p, p->fvec, field, cnt);
+    if (rc) return rc;
+    const size_t need = (size_t)kProfileChunk * nx * 4 * p->csz;   // 8 reals per column
+    if (p->mtab_cap < need) {
+        cudaStreamSynchronize(p->stream);
+        dfree(p->mtab);
+        p->mtab = nullptr;
+        p->mtab_cap = 0;
+        rc = dalloc(&p->mtab, need, "mixing matrices");
+        if (rc) return rc;
+        p->mtab_cap = need;
+    }
+    return SOP_OK;
+}
+
+// Per-column merged mixing of rows P0 .. P1-1 into p->mtab (profile_row reads it).
+int profile_rows(sop_plan p, int64_t n, double dt, int64_t P0, int64_t P1) {
+    const int64_t nx = p->dims[0];
     const int nd = p->ndim;
     const double hbar = p->prm.hbar;
-    auto sample = [&](int64_t s, int a) -> double {
-        return (field && s >= 0 && s < n) ? field[s * nd + a] : 0.0;
-    };
-    // Dirac with a column-dependent vector potential: the samples go to the
-    // device once per call, the merged mixing matrices per chunk of steps.
-    const bool prof = p->comps == 4 && p->profile && field;
-    const int64_t nx = p->dims[0];
-    if (prof) {
-        const int64_t cnt = n * per_step;
-        if (p->fvec_cap < cnt) {
-            cudaStreamSynchronize(p->stream);
-            dfree(p->fvec);
-            p->fvec = nullptr;
-            p->fvec_cap = 0;
-            rc = dalloc(&p->fvec, (size_t)cnt * sizeof(double), "field samples");
-            if (rc) return rc;
-            p->fvec_cap = cnt;
-        }
-        rc = upload(p, p->fvec, field, cnt);
-        if (rc) return rc;
-        const size_t need = (size_t)kProfileChunk * nx * 4 * p->csz;   // 8 reals per column
-        if (p->mtab_cap < need) {
-            cudaStreamSynchronize(p->stream);
-            dfree(p->mtab);
-            p->mtab = nullptr;
-            p->mtab_cap = 0;
-            rc = dalloc(&p->mtab, need, "mixing matrices");
-            if (rc) return rc;
-            p->mtab_cap = need;
-        }
-    }
-    auto mix_rows = [&](int64_t P0, int64_t P1) -> int {   // rows P0 .. P1-1 into p->mtab
-        Bracket br(p, 4);
-        cudaError_t e = build_mix_rows(p->mtab, p->fvec, P0, P1 - P0, nx, nd, n, p->prm.charge, p->prm.c, hbar, dt,
-                                       p->f64, p->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "mixing matrices");
-        br.done();
-        return SOP_OK;
-    };
-    auto mix_row = [&](int64_t P, int64_t P0) -> const void * {
-        return static_cast<const char *>(p->mtab) + (size_t)(P - P0) * nx * 4 * p->csz;
-    };
+    Bracket br(p, 4);
+    cudaError_t e = build_mix_rows(p->mtab, p->fvec, P0, P1 - P0, nx, nd, n, p->prm.charge, p->prm.c, hbar, dt,
+                                   p->f64, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mixing matrices");
+    br.done();
+    return SOP_OK;
+}
 
-    if (prof && nd == 2) {
-        // ---- Dirac, 2D, column-dependent A: the mixing runs as its own
-        // streaming pass between the x transforms of the four components;
-        // the momentum-space factor stays fused in the y pass of the pairs.
-        for (int64_t P0 = 0; P0 <= n; P0 += kProfileChunk) {
-            const int64_t P1 = std::min<int64_t>(n + 1, P0 + kProfileChunk);
-            if ((rc = mix_rows(P0, P1))) return rc;
-            for (int64_t P = P0; P < P1; ++P) {
-                const bool smp = step_sampled(p, P);
-                if (P > 0) {
-                    PassArgs a;
-                    base_args(p, a, p->psi, 0);
-                    a.n_batch = 4;
-                    a.pre = +1;
-                    a.op = OP_NONE;
-                    if ((rc = run_pass(p, a, 1, 2, "Dirac inverse x transform", smp))) return rc;
-                }
-                {
-                    Bracket br(p, 0, smp);
-                    cudaError_t e = launch_dirac3_real(p->psi, p->npts,
-                                                       p->v_set ? ((P == 0 || P == n) ? p->vhalf : p->vfull) : nullptr,
-                                                       nullptr, mix_row(P, P0), nx, p->f64, p->stream);
-                    if (e != cudaSuccess) return cuda_fail(e, "Dirac real-space factor");
-                    br.done();
-                }
-                if (P == n) break;
+const void *profile_row(sop_plan p, int64_t P, int64_t P0) {
+    return static_cast<const char *>(p->mtab) + (size_t)(P - P0) * p->dims[0] * 4 * p->csz;
+}
+
+// Dirac, 2D, vector potential varying along x_1.
+int step_dirac2d_profile(sop_plan p, int64_t n, double dt) {
+    const int64_t nx = p->dims[0];
+    int rc = SOP_OK;
+    // ---- Dirac, 2D, column-dependent A: the mixing runs as its own
+    // streaming pass between the x transforms of the four components;
+    // the momentum-space factor stays fused in the y pass of the pairs.
+    for (int64_t P0 = 0; P0 <= n; P0 += kProfileChunk) {
+        const int64_t P1 = std::min<int64_t>(n + 1, P0 + kProfileChunk);
+        if ((rc = profile_rows(p, n, dt, P0, P1))) return rc;
+        for (int64_t P = P0; P < P1; ++P) {
+            const bool smp = step_sampled(p, P);
+            if (P > 0) {
                 PassArgs a;
                 base_args(p, a, p->psi, 0);
                 a.n_batch = 4;
-                a.pre = -1;
+                a.pre = +1;
                 a.op = OP_NONE;
-                if ((rc = run_pass(p, a, 1, 2, "Dirac forward x transform", smp))) return rc;
-                PassArgs k;
-                base_args(p, k, p->psi, 1);
-                k.pre = -1;
-                k.post = +1;
-                k.op = OP_DT;
-                k.dtab = p->dtab;
-                if ((rc = run_pass(p, k, 2, 1, "Dirac momentum-space pass", smp))) return rc;
+                if ((rc = run_pass(p, a, 1, 2, "Dirac inverse x transform", smp))) return rc;
             }
-        }
-        return SOP_OK;
-    }
-
-    if (p->comps == 2) {
-        // ---- Dirac, 1D, two components: whole steps on chip ----------------
-        // merged mixing M_P = R(A_P) R(A_{P-1}), R(A) = cos th + i sin th sigma_x,
-        // th = q c A tau / (2 hbar) (the half-step factor; A = 0 beyond the call)
-        auto R = [&](int64_t s, cd M[2][2]) {
-            const double th = (field && s >= 0 && s < n) ? 0.5 * p->prm.charge * p->prm.c * field[s] * dt / hbar : 0.0;
-            M[0][0] = M[1][1] = std::cos(th);
-            M[0][1] = M[1][0] = cd(0.0, std::sin(th));
-        };
-        const size_t row_bytes = 4 * p->csz;
-        const size_t bytes = (size_t)(n + 1) * row_bytes;
-        if (p->mtab_cap < bytes) {
-            cudaStreamSynchronize(p->stream);
-            dfree(p->mtab);
-            p->mtab = nullptr;
-            p->mtab_cap = 0;
-            rc = dalloc(&p->mtab, bytes, "Dirac mixing rows");
-            if (rc) return rc;
-            p->mtab_cap = bytes;
-        }
-        std::vector<double> packed(bytes / sizeof(double));
-        for (int64_t P = 0; P <= n; ++P) {
-            cd Rn[2][2], Rp[2][2];
-            R(P, Rn);
-            R(P - 1, Rp);
-            cd M[4];
-            for (int i = 0; i < 2; ++i)
-                for (int j = 0; j < 2; ++j) M[2 * i + j] = Rn[i][0] * Rp[0][j] + Rn[i][1] * Rp[1][j];
-            for (int q = 0; q < 4; ++q) {
-                if (p->f64) {
-                    packed[(size_t)P * 8 + 2 * q] = M[q].real();
-                    packed[(size_t)P * 8 + 2 * q + 1] = M[q].imag();
-                } else {
-                    float *f = reinterpret_cast<float *>(packed.data() + (size_t)P * 4);
-                    f[2 * q] = (float)M[q].real();
-                    f[2 * q + 1] = (float)M[q].imag();
-                }
-            }
-        }
-        rc = upload(p, static_cast<double *>(p->mtab), packed.data(), (int64_t)packed.size());
-        if (rc) return rc;
-        Args1D a1{};
-        a1.psi = p->psi;
-        a1.n_rows = 1;
-        a1.n_steps = n;
-        a1.p_begin = 0;
-        a1.p_end = n + 1;
-        a1.p_table0 = 0;
-        a1.tw = p->tw[0];
-        a1.vhalf = p->v_set ? p->vhalf : nullptr;
-        a1.vfull = p->v_set ? p->vfull : nullptr;
-        a1.mtab = p->mtab;
-        a1.dtab = p->dtab;
-        a1.scale_hi = p->scale_hi;
-        a1.scale_lo = p->scale_lo;
-        Bracket br(p, 3);
-        cudaError_t e = p->f64 ? launch_1d_dirac_f64(a1, (int)p->dims[0], p->stream)
-                               : launch_1d_dirac_f32(a1, (int)p->dims[0], p->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "1D Dirac step kernel");
-        br.done();
-        return SOP_OK;
-    }
-
-    if (p->comps == 4 && nd == 3) {
-        // ---- Dirac, 3D: the 4x4 factors couple all components ---------------
-        // Per real-space index P: exp(-i V tau') M_P with M_P = R(A_P) R(A_{P-1}),
-        // then (P < n) the forward transforms of all four components along x,
-        // y, z, the momentum-space factor, the inverse transforms.
-        cd al[3][4][4];
-        for (int a = 0; a < 3; ++a)
-            for (int i = 0; i < 4; ++i)
-                for (int j = 0; j < 4; ++j) al[a][i][j] = 0.0;
-        al[0][0][3] = al[0][1][2] = al[0][2][1] = al[0][3][0] = 1.0;   // alpha_1 (Dirac representation)
-        al[1][0][3] = cd(0, -1);                                        // alpha_2
-        al[1][1][2] = cd(0, 1);
-        al[1][2][1] = cd(0, -1);
-        al[1][3][0] = cd(0, 1);
-        al[2][0][2] = 1.0;                                              // alpha_3
-        al[2][1][3] = -1.0;
-        al[2][2][0] = 1.0;
-        al[2][3][1] = -1.0;
-        // R(A) = cos th + i sin th sum_a (Abar_a/Abar) alpha_a with Abar_a = A_a tau and
-        // th = q c Abar / (2 hbar) (Eq. 26 with delta = 1/2; identity for A = 0)
-        auto R = [&](int64_t s, cd M[4][4]) {
-            double Ab[3] = {0, 0, 0}, mag = 0.0;
-            for (int a = 0; a < 3; ++a) {
-                Ab[a] = prof ? 0.0 : sample(s, a) * dt;   // (per-column matrices come from mix_rows)
-                mag += Ab[a] * Ab[a];
-            }
-            mag = std::sqrt(mag);
-            const double th = 0.5 * p->prm.charge * p->prm.c * mag / hbar;
-            for (int i = 0; i < 4; ++i)
-                for (int j = 0; j < 4; ++j) {
-                    cd v = (i == j) ? cd(std::cos(th), 0.0) : cd(0.0, 0.0);
-                    if (mag > 0)
-                        for (int a = 0; a < 3; ++a) v += cd(0.0, std::sin(th)) * (Ab[a] / mag) * al[a][i][j];
-                    M[i][j] = v;
-                }
-        };
-        int64_t P0 = 0;
-        for (int64_t P = 0; P <= n; ++P) {
-            if (prof && (P - P0 == kProfileChunk || P == 0)) {
-                P0 = P;
-                if ((rc = mix_rows(P0, std::min<int64_t>(n + 1, P0 + kProfileChunk)))) return rc;
-            }
-            cd Rn[4][4], Rp[4][4];
-            R(P, Rn);
-            R(P - 1, Rp);
-            double Md[32];
-            for (int i = 0; i < 4; ++i)
-                for (int j = 0; j < 4; ++j) {
-                    cd v = 0.0;
-                    for (int k = 0; k < 4; ++k) v += Rn[i][k] * Rp[k][j];
-                    Md[2 * (4 * i + j)] = v.real();
-                    Md[2 * (4 * i + j) + 1] = v.imag();
-                }
-            const bool smp = step_sampled(p, P);
             {
                 Bracket br(p, 0, smp);
-                cudaError_t e = launch_dirac3_real(p->psi, p->npts, p->v_set ? ((P == 0 || P == n) ? p->vhalf : p->vfull)
-                                                                             : nullptr,
-                                                   prof ? nullptr : Md, prof ? mix_row(P, P0) : nullptr, nx, p->f64,
-                                                   p->stream);
-                if (e != cudaSuccess) return cuda_fail(e, "3D Dirac real-space factor");
+                cudaError_t e = launch_dirac3_real(p->psi, p->npts,
+                                                   p->v_set ? ((P == 0 || P == n) ? p->vhalf : p->vfull) : nullptr,
+                                                   nullptr, profile_row(p, P, P0), nx, p->f64, p->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "Dirac real-space factor");
                 br.done();
             }
             if (P == n) break;
-            for (int ax = 0; ax < 3; ++ax) {
-                PassArgs a;
-                base_args(p, a, p->psi, ax);
-                a.n_batch = 4;
-                a.pre = -1;
-                a.op = OP_NONE;
-                rc = run_pass(p, a, 1, 2, "3D Dirac forward transform", smp);
-                if (rc) return rc;
-            }
-            {
-                Bracket br(p, 1, smp);
-                cudaError_t e = launch_dirac3_kinetic(p->psi, p->npts, p->dtab, p->scale_hi, p->scale_lo, p->f64,
-                                                      p->stream);
-                if (e != cudaSuccess) return cuda_fail(e, "3D Dirac momentum-space factor");
-                br.done();
-            }
-            for (int ax = 2; ax >= 0; --ax) {
-                PassArgs a;
-                base_args(p, a, p->psi, ax);
-                a.n_batch = 4;
-                a.pre = +1;
-                a.op = OP_NONE;
-                rc = run_pass(p, a, 1, 2, "3D Dirac inverse transform", smp);
-                if (rc) return rc;
-            }
-        }
-        return SOP_OK;
-    }
-
-    if (p->comps == 4) {
-        // ---- Dirac, 2D, component pairs ------------------------------------
-        for (int64_t P = 0; P <= n; ++P) {
             PassArgs a;
             base_args(p, a, p->psi, 0);
-            a.pre = P > 0 ? +1 : 0;
-            a.post = P < n ? -1 : 0;
-            a.op = OP_DV;
-            a.vtab = p->v_set ? ((P == 0 || P == n) ? p->vhalf : p->vfull) : nullptr;
-            cd Rn[2][2][2], Rp[2][2][2];
-            double An[2] = {sample(P, 0), sample(P, 1)};
-            double Ap[2] = {sample(P - 1, 0), sample(P - 1, 1)};
-            mixing_blocks(p, (field && P < n) ? An : nullptr, dt, Rn);
-            mixing_blocks(p, (field && P > 0) ? Ap : nullptr, dt, Rp);
-            for (int pr = 0; pr < 2; ++pr) {
-                // M = R(A_P) R(A_{P-1}): trailing half of step P-1 first.
-                cd M[2][2];
-                for (int i = 0; i < 2; ++i)
-                    for (int j = 0; j < 2; ++j) M[i][j] = Rn[pr][i][0] * Rp[pr][0][j] + Rn[pr][i][1] * Rp[pr][1][j];
-                for (int i = 0; i < 2; ++i)
-                    for (int j = 0; j < 2; ++j) {
-                        a.mix[pr][2 * (2 * i + j)] = M[i][j].real();
-                        a.mix[pr][2 * (2 * i + j) + 1] = M[i][j].imag();
-                    }
-            }
-            rc = run_pass(p, a, 2, 0, "Dirac real-space pass", step_sampled(p, P));
-            if (rc) return rc;
-            if (P < n) {
-                PassArgs k;
-                base_args(p, k, p->psi, 1);
-                k.pre = -1;
-                k.post = +1;
-                k.op = OP_DT;
-                k.dtab = p->dtab;
-                rc = run_pass(p, k, 2, 1, "Dirac momentum-space pass", step_sampled(p, P));
-                if (rc) return rc;
+            a.n_batch = 4;
+            a.pre = -1;
+            a.op = OP_NONE;
+            if ((rc = run_pass(p, a, 1, 2, "Dirac forward x transform", smp))) return rc;
+            PassArgs k;
+            base_args(p, k, p->psi, 1);
+            k.pre = -1;
+            k.post = +1;
+            k.op = OP_DT;
+            k.dtab = p->dtab;
+            if ((rc = run_pass(p, k, 2, 1, "Dirac momentum-space pass", smp))) return rc;
+        }
+    }
+    return SOP_OK;
+}
+
+// Dirac, 1D, two components.
+int step_dirac1d(sop_plan p, int64_t n, double dt, const double *field) {
+    const double hbar = p->prm.hbar;
+    int rc = SOP_OK;
+    // ---- Dirac, 1D, two components: whole steps on chip ----------------
+    // merged mixing M_P = R(A_P) R(A_{P-1}), R(A) = cos th + i sin th sigma_x,
+    // th = q c A tau / (2 hbar) (the half-step factor; A = 0 beyond the call)
+    auto R = [&](int64_t s, cd M[2][2]) {
+        const double th = (field && s >= 0 && s < n) ? 0.5 * p->prm.charge * p->prm.c * field[s] * dt / hbar : 0.0;
+        M[0][0] = M[1][1] = std::cos(th);
+        M[0][1] = M[1][0] = cd(0.0, std::sin(th));
+    };
+    const size_t row_bytes = 4 * p->csz;
+    const size_t bytes = (size_t)(n + 1) * row_bytes;
+    if (p->mtab_cap < bytes) {
+        cudaStreamSynchronize(p->stream);
+        dfree(p->mtab);
+        p->mtab = nullptr;
+        p->mtab_cap = 0;
+        rc = dalloc(&p->mtab, bytes, "Dirac mixing rows");
+        if (rc) return rc;
+        p->mtab_cap = bytes;
+    }
+    std::vector<double> packed(bytes / sizeof(double));
+    for (int64_t P = 0; P <= n; ++P) {
+        cd Rn[2][2], Rp[2][2];
+        R(P, Rn);
+        R(P - 1, Rp);
+        cd M[4];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) M[2 * i + j] = Rn[i][0] * Rp[0][j] + Rn[i][1] * Rp[1][j];
+        for (int q = 0; q < 4; ++q) {
+            if (p->f64) {
+                packed[(size_t)P * 8 + 2 * q] = M[q].real();
+                packed[(size_t)P * 8 + 2 * q + 1] = M[q].imag();
+            } else {
+                float *f = reinterpret_cast<float *>(packed.data() + (size_t)P * 4);
+                f[2 * q] = (float)M[q].real();
+                f[2 * q + 1] = (float)M[q].imag();
             }
         }
-        return SOP_OK;
     }
+    rc = upload(p, static_cast<double *>(p->mtab), packed.data(), (int64_t)packed.size());
+    if (rc) return rc;
+    Args1D a1{};
+    a1.psi = p->psi;
+    a1.n_rows = 1;
+    a1.n_steps = n;
+    a1.p_begin = 0;
+    a1.p_end = n + 1;
+    a1.p_table0 = 0;
+    a1.tw = p->tw[0];
+    a1.vhalf = p->v_set ? p->vhalf : nullptr;
+    a1.vfull = p->v_set ? p->vfull : nullptr;
+    a1.mtab = p->mtab;
+    a1.dtab = p->dtab;
+    a1.scale_hi = p->scale_hi;
+    a1.scale_lo = p->scale_lo;
+    Bracket br(p, 3);
+    cudaError_t e = p->f64 ? launch_1d_dirac_f64(a1, (int)p->dims[0], p->stream)
+                           : launch_1d_dirac_f32(a1, (int)p->dims[0], p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "1D Dirac step kernel");
+    br.done();
+    return SOP_OK;
+}
 
-    // ---- Schroedinger -------------------------------------------------------
+// Dirac, 3D, four components; prof: per-column mixing rows instead of a uniform A.
+int step_dirac3d(sop_plan p, int64_t n, double dt, const double *field, bool prof) {
+    const int64_t nx = p->dims[0];
+    const double hbar = p->prm.hbar;
+    int rc = SOP_OK;
+    // ---- Dirac, 3D: the 4x4 factors couple all components ---------------
+    // Per real-space index P: exp(-i V tau') M_P with M_P = R(A_P) R(A_{P-1}),
+    // then (P < n) the forward transforms of all four components along x,
+    // y, z, the momentum-space factor, the inverse transforms.
+    cd al[3][4][4];
+    for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) al[a][i][j] = 0.0;
+    al[0][0][3] = al[0][1][2] = al[0][2][1] = al[0][3][0] = 1.0;   // alpha_1 (Dirac representation)
+    al[1][0][3] = cd(0, -1);                                        // alpha_2
+    al[1][1][2] = cd(0, 1);
+    al[1][2][1] = cd(0, -1);
+    al[1][3][0] = cd(0, 1);
+    al[2][0][2] = 1.0;                                              // alpha_3
+    al[2][1][3] = -1.0;
+    al[2][2][0] = 1.0;
+    al[2][3][1] = -1.0;
+    // R(A) = cos th + i sin th sum_a (Abar_a/Abar) alpha_a with Abar_a = A_a tau and
+    // th = q c Abar / (2 hbar) (Eq. 26 with delta = 1/2; identity for A = 0)
+    auto R = [&](int64_t s, cd M[4][4]) {
+        double Ab[3] = {0, 0, 0}, mag = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            Ab[a] = prof ? 0.0 : field_sample(field, n, 3, s, a) * dt;   // (per-column: profile_rows)
+            mag += Ab[a] * Ab[a];
+        }
+        mag = std::sqrt(mag);
+        const double th = 0.5 * p->prm.charge * p->prm.c * mag / hbar;
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+                cd v = (i == j) ? cd(std::cos(th), 0.0) : cd(0.0, 0.0);
+                if (mag > 0)
+                    for (int a = 0; a < 3; ++a) v += cd(0.0, std::sin(th)) * (Ab[a] / mag) * al[a][i][j];
+                M[i][j] = v;
+            }
+    };
+    int64_t P0 = 0;
+    for (int64_t P = 0; P <= n; ++P) {
+        if (prof && (P - P0 == kProfileChunk || P == 0)) {
+            P0 = P;
+            if ((rc = profile_rows(p, n, dt, P0, std::min<int64_t>(n + 1, P0 + kProfileChunk)))) return rc;
+        }
+        cd Rn[4][4], Rp[4][4];
+        R(P, Rn);
+        R(P - 1, Rp);
+        double Md[32];
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+                cd v = 0.0;
+                for (int k = 0; k < 4; ++k) v += Rn[i][k] * Rp[k][j];
+                Md[2 * (4 * i + j)] = v.real();
+                Md[2 * (4 * i + j) + 1] = v.imag();
+            }
+        const bool smp = step_sampled(p, P);
+        {
+            Bracket br(p, 0, smp);
+            cudaError_t e = launch_dirac3_real(p->psi, p->npts, p->v_set ? ((P == 0 || P == n) ? p->vhalf : p->vfull)
+                                                                         : nullptr,
+                                               prof ? nullptr : Md, prof ? profile_row(p, P, P0) : nullptr, nx, p->f64,
+                                               p->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "3D Dirac real-space factor");
+            br.done();
+        }
+        if (P == n) break;
+        for (int ax = 0; ax < 3; ++ax) {
+            PassArgs a;
+            base_args(p, a, p->psi, ax);
+            a.n_batch = 4;
+            a.pre = -1;
+            a.op = OP_NONE;
+            rc = run_pass(p, a, 1, 2, "3D Dirac forward transform", smp);
+            if (rc) return rc;
+        }
+        {
+            Bracket br(p, 1, smp);
+            cudaError_t e = launch_dirac3_kinetic(p->psi, p->npts, p->dtab, p->scale_hi, p->scale_lo, p->f64,
+                                                  p->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "3D Dirac momentum-space factor");
+            br.done();
+        }
+        for (int ax = 2; ax >= 0; --ax) {
+            PassArgs a;
+            base_args(p, a, p->psi, ax);
+            a.n_batch = 4;
+            a.pre = +1;
+            a.op = OP_NONE;
+            rc = run_pass(p, a, 1, 2, "3D Dirac inverse transform", smp);
+            if (rc) return rc;
+        }
+    }
+    return SOP_OK;
+}
+
+// Dirac, 2D, four components as the component pairs (1,4) and (2,3).
+int step_dirac2d(sop_plan p, int64_t n, double dt, const double *field) {
+    int rc = SOP_OK;
+    // ---- Dirac, 2D, component pairs ------------------------------------
+    for (int64_t P = 0; P <= n; ++P) {
+        PassArgs a;
+        base_args(p, a, p->psi, 0);
+        a.pre = P > 0 ? +1 : 0;
+        a.post = P < n ? -1 : 0;
+        a.op = OP_DV;
+        a.vtab = p->v_set ? ((P == 0 || P == n) ? p->vhalf : p->vfull) : nullptr;
+        cd Rn[2][2][2], Rp[2][2][2];
+        double An[2] = {field_sample(field, n, 2, P, 0), field_sample(field, n, 2, P, 1)};
+        double Ap[2] = {field_sample(field, n, 2, P - 1, 0), field_sample(field, n, 2, P - 1, 1)};
+        mixing_blocks(p, (field && P < n) ? An : nullptr, dt, Rn);
+        mixing_blocks(p, (field && P > 0) ? Ap : nullptr, dt, Rp);
+        for (int pr = 0; pr < 2; ++pr) {
+            // M = R(A_P) R(A_{P-1}): trailing half of step P-1 first.
+            cd M[2][2];
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j) M[i][j] = Rn[pr][i][0] * Rp[pr][0][j] + Rn[pr][i][1] * Rp[pr][1][j];
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j) {
+                    a.mix[pr][2 * (2 * i + j)] = M[i][j].real();
+                    a.mix[pr][2 * (2 * i + j) + 1] = M[i][j].imag();
+                }
+        }
+        rc = run_pass(p, a, 2, 0, "Dirac real-space pass", step_sampled(p, P));
+        if (rc) return rc;
+        if (P < n) {
+            PassArgs k;
+            base_args(p, k, p->psi, 1);
+            k.pre = -1;
+            k.post = +1;
+            k.op = OP_DT;
+            k.dtab = p->dtab;
+            rc = run_pass(p, k, 2, 1, "Dirac momentum-space pass", step_sampled(p, P));
+            if (rc) return rc;
+        }
+    }
+    return SOP_OK;
+}
+
+// Schroedinger, 1D/2D/3D, length or velocity gauge.
+int step_schrodinger(sop_plan p, int64_t n, double dt, const double *field) {
+    const int nd = p->ndim;
+    int rc = SOP_OK;
     FieldRows fr;
     rc = prepare_fields(p, n, dt, field, fr);
     if (rc) return rc;
@@ -947,6 +958,26 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
         }
     }
     return SOP_OK;
+}
+
+int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
+    if (!p) return fail(SOP_EINVAL, "sop_step: null plan");
+    if (!p->psi) return fail(SOP_ESTATE, "sop_step: no state bound (call sop_bind_state first)");
+    if (n < 0) return fail(SOP_EINVAL, "sop_step: n_steps < 0");
+    if (!is_finite(dt)) return fail(SOP_EINVAL, "sop_step: dt is not finite");
+    if (n == 0) return SOP_OK;
+    const int64_t per_step = (int64_t)p->ndim * (p->profile ? p->dims[0] : 1);   // samples per step
+    if (field)
+        for (int64_t i = 0; i < n * per_step; ++i)
+            if (!is_finite(field[i])) return fail(SOP_EINVAL, "sop_step: field sample is not finite");
+    int rc = ensure_tables(p, dt);
+    if (rc) return rc;
+    const bool prof = p->comps == 4 && p->profile && field;
+    if (prof && (rc = prepare_profile(p, n, field))) return rc;
+    if (p->comps == 2) return step_dirac1d(p, n, dt, field);
+    if (p->comps == 4 && p->ndim == 3) return step_dirac3d(p, n, dt, field, prof);
+    if (p->comps == 4) return prof ? step_dirac2d_profile(p, n, dt) : step_dirac2d(p, n, dt, field);
+    return step_schrodinger(p, n, dt, field);
 }
 
 int read_result(sop_plan p, int count, double *out) {
