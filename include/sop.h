@@ -137,7 +137,8 @@ int sop_set_gauge(sop_plan plan, int gauge);
 /* Advance the bound state by n_steps Strang steps of size dt (Eq. 8).  The
  * real-space factors of adjacent steps are merged (exact algebra): the call
  * applies one half real-space factor at its start and one at its end.
- * field_samples: host array of n_steps*ndim doubles or NULL (see above).
+ * field_samples: host array of n_steps*ndim doubles or NULL (see above);
+ * n_steps*dims[0]*ndim for a Dirac plan after sop_set_field_profile(plan, 1).
  * Asynchronous on the plan stream.  n_steps = 0 is a no-op.  Returns
  * SOP_ESTATE if no state is bound. */
 int sop_step(sop_plan plan, int64_t n_steps, double dt, const double *field_samples);
