@@ -20,19 +20,23 @@ import numpy as np
 from . import schrodinger_propagate
 
 
-def spectral(psi0, V, spacing, dt, n_steps, energies, mass=1.0, hbar=1.0):
-    """Returns (chi [N+1], spectrum [K], psi_E [K, ...shape]) for the energies E_k."""
+def spectral(psi0, V, spacing, dt, n_steps, energies, mass=1.0, hbar=1.0, propagate=None):
+    """Returns (chi [N+1], spectrum [K], psi_E [K, ...shape]) for the energies E_k.
+    propagate(psi, dt) -> psi advances one step (default: the oracle's
+    Schroedinger step); for a spinor the sums run over all components and
+    dV is the product of the spatial spacings."""
     psi0 = np.asarray(psi0, dtype=np.complex128)
     E = np.atleast_1d(np.asarray(energies, dtype=np.float64))
     N = int(n_steps)
     T = N * dt
-    dV = float(np.prod(spacing[:psi0.ndim]))
+    dV = float(np.prod(spacing))
     chi = np.zeros(N + 1, dtype=np.complex128)
     acc = np.zeros((len(E),) + psi0.shape, dtype=np.complex128)
     psi = psi0
     for n in range(N + 1):
         if n > 0:
-            psi = schrodinger_propagate(psi, V, spacing, dt, 1, None, mass=mass, hbar=hbar)
+            psi = (propagate(psi, dt) if propagate is not None
+                   else schrodinger_propagate(psi, V, spacing, dt, 1, None, mass=mass, hbar=hbar))
         t = n * dt
         chi[n] = dV * np.vdot(psi0, psi)
         w = 1.0 - np.cos(2.0 * np.pi * t / T)

@@ -97,3 +97,23 @@ def test_window_and_unitarity():
     assert abs(win[0]) < 1e-15 and abs(win[-1]) < 1e-12
     ref = dt * np.sum((chi * win * np.exp(1j * t * 0.3))[1:-1])
     assert abs(spec[0] - ref) < 1e-12
+
+
+def test_dirac_plane_wave_spectrum():
+    """Spinor form: a positive-energy 1D Dirac plane wave has chi_n =
+    exp(-i E t_n) exactly and the spectrum peaks at E (the window is symmetric
+    about it on a grid centred there)."""
+    import oracle
+    oracle.build()
+    n, h, c = 64, 0.02, 137.036
+    p0 = 2 * np.pi * 3 / (n * h)
+    E = np.sqrt(c ** 4 + c * c * p0 * p0)
+    v = np.conj(oracle.dirac1d_u(p0)[0])
+    x = wl.lattice(n, h)
+    psi0 = np.stack([vk * np.exp(1j * p0 * x) for vk in v]) / np.sqrt(n * h)
+    dt, N = 2e-4, 60
+    Es = E + np.linspace(-400.0, 400.0, 81)
+    chi, spec, _ = osp.spectral(psi0, None, (h,), dt, N, Es,
+                                propagate=lambda s, t: oracle.dirac1d_propagate(s, None, (h,), t, 1))
+    assert np.abs(chi - np.exp(-1j * E * dt * np.arange(N + 1))).max() < 1e-11
+    assert abs(osp.peak(Es, spec) - E) < 1e-6 * E
