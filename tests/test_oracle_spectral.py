@@ -29,6 +29,30 @@ def test_plane_wave_autocorrelation_is_exact():
     assert np.abs(chi - np.exp(-0.5j * k * k * t)).max() < 1e-12
 
 
+def test_eigenfunction_of_an_exact_eigenstate_is_absolute():
+    """A lattice plane wave is an exact eigenvector of the free split step,
+    psi_n = exp(-i E0 t_n) psi_0 with E0 = k^2/2, so the accumulated
+    eigenfunction has a closed form that fixes its dt factor, window weights
+    and phase sign (not only its direction):
+      Psi_{E0}            = dt sum_n w_n psi_0 = N dt psi_0 = T psi_0,
+      Psi_{E0 + 2 pi / T} = -T/2 psi_0,
+      Psi_{E0 + 4 pi / T} = 0,
+    since sum_{n=0}^{N} (1 - cos(2 pi n/N)) exp(2 pi i m n/N) = N, -N/2, 0 for
+    m = 0, 1, 2 (N > 4)."""
+    n, L, dt, N = 64, 20.0, 0.05, 40
+    T = N * dt
+    x = wl.lattice(n, L / n)
+    k = 2 * np.pi * 3 / L
+    psi0 = np.exp(1j * k * x) / np.sqrt(L)
+    E0 = 0.5 * k * k
+    Es = [E0, E0 + 2 * np.pi / T, E0 + 4 * np.pi / T]
+    _, _, psiE = osp.spectral(psi0, np.zeros(n), (L / n,), dt, N, Es)
+    scale = T * np.abs(psi0).max()
+    assert np.abs(psiE[0] - T * psi0).max() < 1e-12 * scale
+    assert np.abs(psiE[1] + 0.5 * T * psi0).max() < 1e-12 * scale
+    assert np.abs(psiE[2]).max() < 1e-12 * scale
+
+
 def test_harmonic_levels():
     """V = w^2 x^2 / 2: peaks at w (k + 1/2)."""
     n, L, w, dt, N = 128, 40.0, 0.5, 0.05, 3000
