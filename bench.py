@@ -57,6 +57,8 @@ def parse_args():
                     help="time the passes of one split step in this many (per-class roofline)")
     ap.add_argument("--batched", type=int, default=1, help="also time the batched, adjoint and spectral forms (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=400, help="split steps of the batched / adjoint / spectral sample")
+    ap.add_argument("--configs", type=int, default=1,
+                    help="also time configs 1, 3, 4 and config 2 in FP64 at full size and length (0: skip)")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
@@ -107,6 +109,111 @@ def ncu_traffic(kernel_class: str):
         return None
     ent = d.get("per_launch_dram_bytes", {}).get(kernel_class)
     return None if ent is None else float(ent)
+
+
+def golden_sample(cfg: int):
+    """The FP64 oracle's final state of a paper-shaped configuration at full
+    size and full step count, on a seeded sample of lattice values, written by
+    tests/golden/make_fullsize.py (oracle and input generators only)."""
+    path = os.path.join(ROOT, "tests", "golden", f"fullsize_config{cfg}.npz")
+    if not os.path.exists(path):
+        return None
+    return np.load(path)
+
+
+def fp64_flop_counts():
+    """FP64 operations per lattice point of each pass class, counted by ncu on
+    the current pass-kernel sources (profiles/fp64_flops.json), or None."""
+    path = os.path.join(ROOT, "profiles", "fp64_flops.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("pass_kernel_hash") != pass_kernel_hash():
+        return None
+    return d
+
+
+def config_legs(args, sop, wl, torch, stream, flush, peak):
+    """Each paper-shaped configuration in its own right: configs 1 (1D, FP64),
+    3 (3D 512^3) and 4 (2D Dirac 1024^2) timed over their full step counts,
+    config 2 in FP64 over its full 5000 steps; every run compared with the
+    FP64 oracle (config 1 in full, the others on the stored oracle sample)."""
+    out = {}
+
+    def run(w, dtype, n_steps=None, tune=True):
+        n = w.n_steps if n_steps is None else n_steps
+        q = sop.Propagator(w.dims, w.spacing, w.comps, dtype,
+                           params=dict(mass=w.mass, charge=w.charge, hbar=w.hbar, c=w.c))
+        if w.V is not None:
+            q.set_potential(w.V)
+        q.set_state(torch.from_numpy(w.psi0))
+        shapes = q.autotune(w.dt, 8) if tune else [0, 0]
+        F = None if w.field is None else np.asarray(w.field)[:n]
+        q.step(min(4, n), w.dt, None if F is None else F[:min(4, n)])   # warm-up
+        q.set_state(torch.from_numpy(w.psi0))
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        q.step(n, w.dt, F)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return q, a.elapsed_time(b) * 1e-3, shapes
+
+    def sampled_err(q, g):
+        idx = torch.from_numpy(g["idx"]).cuda()
+        got = q.state.reshape(-1)[idx].to(torch.complex128).cpu().numpy()
+        ref = g["values"]
+        return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+    # config 1: 1D harmonic coherent state, plain FP64 path, whole line on chip
+    import oracle
+    w1 = wl.config1()
+    q, t, _ = run(w1, "c128", tune=False)
+    ref1 = oracle.schrodinger_propagate(w1.psi0, w1.V, w1.spacing, w1.dt, w1.n_steps)
+    got1 = q.state.cpu().numpy()
+    out["1"] = {"value": w1.npoints * w1.n_steps / t, "unit": UNIT, "dtype": "f64",
+                "workload": "1D Schroedinger N=1024 on [-100,100), harmonic V (omega 0.1), coherent packet "
+                            "x0=-20, dt 0.05, 2000 steps", "us_per_step": t / w1.n_steps * 1e6,
+                "roofline": "n/a: the whole line stays on chip across steps (latency-bound, one CTA)",
+                "err_vs_oracle": {"f64": float(np.linalg.norm(got1 - ref1) / np.linalg.norm(ref1)),
+                                  "compared": "full state after 2000 steps"}}
+    q.close()
+
+    flops = fp64_flop_counts()
+    for cfg, make, b_per_pt in ((4, wl.config4, 4 * 32 + 4), (3, wl.config3, 4 * 8 + 4), (2, wl.config2, 4 * 8 + 4)):
+        w = make()
+        g = golden_sample(cfg)
+        leg = {"workload": w.name, "lattice": list(w.dims), "components": w.comps, "split_steps": w.n_steps}
+        for dtype in (("c128",) if cfg == 2 else ("c64", "c128")):
+            q, t, shapes = run(w, dtype)
+            key = {"c64": "f32", "c128": "f64"}[dtype]
+            ent = {"value": w.npoints * w.n_steps / t, "unit": UNIT, "us_per_step": t / w.n_steps * 1e6,
+                   "pass_shapes": shapes}
+            if dtype == "c64":
+                bmin = b_per_pt * w.npoints
+                ent["roofline"] = {"bound": "hbm", "step_b_min_bytes": bmin,
+                                   "achieved": bmin / (t / w.n_steps) / 1e9, "peak": peak, "unit": "GB/s",
+                                   "frac": bmin / (t / w.n_steps) / 1e9 / peak}
+            elif flops is not None and cfg in (2, 4):
+                key_f = {2: "schrodinger_2d", 4: "dirac_2d"}[cfg]
+                fpp = flops.get("flops_per_point_step", {}).get(key_f)
+                fpk = flops.get("fp64_fma_peak_tflops")
+                if fpp:
+                    ach = fpp * w.npoints / (t / w.n_steps) / 1e12
+                    ent["roofline"] = {"bound": "alu", "achieved": ach, "unit": "TFLOP/s",
+                                       "flops_per_point_step": fpp, "peak": fpk,
+                                       "frac": None if not fpk else ach / fpk,
+                                       "peak_source": "sop_fma_peak (FP64 FMA chains, measured in this run)"}
+            if g is not None:
+                ent["err_vs_oracle"] = sampled_err(q, g)
+                ent["norm"] = q.norm()
+                ent["oracle_norm"] = float(g["norm"])
+            leg[key] = ent
+            q.close()
+            torch.cuda.empty_cache()
+        out[str(cfg)] = leg
+    return out
 
 
 class ClockSampler:
@@ -225,6 +332,8 @@ def main():
     prop = sop.Propagator(w.dims, w.spacing, 1, "c64")
     psi0 = torch.from_numpy(w.psi0.astype(np.complex64)).cuda()
     prop.set_potential(w.V)
+    prop.state.copy_(psi0)
+    pass_shapes = prop.autotune(w.dt, 16)   # launch shapes of the x and y passes (untimed)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def one_step(ev=None):
@@ -501,6 +610,20 @@ def main():
         qp.close()
         torch.cuda.empty_cache()
 
+    # ---- every configuration at full size and full step count ---------------
+    configs = None
+    fma_peaks = None
+    if args.configs and rank == 0:
+        fma_peaks = {"f64_tflops": sop.sop_fma_peak(True) / 1e12, "f32_tflops": sop.sop_fma_peak(False) / 1e12,
+                     "how": "sop_fma_peak: 8 independent FMA chains per thread, 8 CTAs x 256 threads per SM, "
+                            "best of 3 launches (CUDA events)"}
+        configs = config_legs(args, sop, wl, torch, stream, flush, measured_peaks()[0])
+        for leg in configs.values():
+            r = leg.get("f64", {}).get("roofline") if isinstance(leg, dict) else None
+            if r and r.get("bound") == "alu":
+                r["peak"] = fma_peaks["f64_tflops"]
+                r["frac"] = r["achieved"] / r["peak"]
+
     # ---- FP64 sample, same lattice -----------------------------------------
     fp64 = None
     if args.fp64_steps > 0:
@@ -590,10 +713,12 @@ def main():
                                    f"sin^2 laser along x, {S} split steps of dt=0.02 per benchmark step",
                        "lattice": [args.n, args.n], "split_steps_per_step": S,
                        "ms_per_split_step": total_ms / args.steps / S,
+                       "pass_shapes": {"x": pass_shapes[0], "y": pass_shapes[1], "chosen_by": "sop_autotune"},
                        "l2": "flushed (256 MiB write) before every timed step; psi + V tables stay L2-resident "
                              "within a step",
                        "parallelism": f"replicas x{world} (independent problems, no data-path collective)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "configs": configs, "fma_peaks": fma_peaks,
             "fp64": fp64, "batched": batched, "adjoint": adjoint, "spectral": spectral, "velocity_gauge": velocity, "dirac1d": dirac1d, "dirac3d": dirac3d, "dirac_profile": dirac_profile, "err_vs_oracle": err, "clocks": clocks,
         }
         s = json.dumps(line)

@@ -185,6 +185,58 @@ int sop_profile_read(sop_plan plan, double *ms, int64_t *launches, int max_class
  * (passes, table set-up and reductions).  Host-side counter; no sync. */
 int64_t sop_launch_counter(sop_plan plan);
 
+/* Launch shapes of the pencil passes (an implementation choice, not part of
+ * the paper's method: every shape computes the same transforms, Sec. 2.1, in
+ * the same operation order, so results are bit-identical across shapes).
+ * A shape fixes the pencils per CTA, the number of tile buffers, where the
+ * stage twiddles and the pass-axis factor row live (shared memory or L1) and
+ * the register budget; SOP_PASS_SHAPES shapes exist, 0 is the default.
+ *
+ * sop_autotune: times every shape of the contiguous-axis pass (x) and then of
+ * the strided-axis passes (y, z) for this plan's lattice, component count
+ * and dtype, over trial_steps split steps of size dt (<= 0: 16) with no
+ * field, and keeps the fastest of each.  The trials run on a scratch copy of
+ * the bound state (allocated like sop_energy's scratch if absent), so the
+ * state is unchanged.  Results are cached per process for the lattice shape,
+ * component count, dtype and device: a later plan of the same shape takes
+ * them without timing.  chosen (may be NULL) receives 2 ints: the shapes of
+ * the contiguous and the strided passes.  Synchronises the plan stream.
+ * One-dimensional plans have no pencil passes (chosen = {0, 0}).
+ * Errors: SOP_EINVAL (null plan), SOP_ESTATE (no state bound), SOP_ECUDA,
+ * SOP_ETIMEOUT.
+ *
+ * sop_set_pass_shape: forces shape `shape` (0 .. SOP_PASS_SHAPES - 1) for the
+ * contiguous (axis_kind 0) or strided (axis_kind 1) passes of this plan.
+ * Sizes without a kernel of that shape use shape 0.  SOP_EINVAL for a bad
+ * argument. */
+#define SOP_PASS_SHAPES 8
+int sop_autotune(sop_plan plan, double dt, int trial_steps, int *chosen);
+int sop_set_pass_shape(sop_plan plan, int axis_kind, int shape);
+
+/* Failure detection of the persistent passes (not part of the paper's
+ * method).  Every wait of a pass kernel for its tile copies is bounded in wall
+ * time (2 s by default, far beyond any copy).  A CTA whose wait runs out
+ * records it in the plan's error word, lets its own copies finish and leaves;
+ * later passes of the stream see the word and do nothing; the next
+ * synchronising call (sop_norm, sop_energy, sop_step_host, ...) returns
+ * SOP_ETIMEOUT and clears the word and the tile counters, after which the
+ * plan steps normally again (the state of the failed call is unfinished).
+ * sop_set_wait_limit sets the limit of the tile-copy waits in ns (0: the
+ * default); a limit of a few ns makes the waits give up while the copies
+ * still complete normally, which is how the error path is tested.
+ * SOP_EINVAL for a null plan. */
+int sop_set_wait_limit(sop_plan plan, uint64_t wait_ns);
+
+/* Measured FMA throughput of the current device (not part of the paper's
+ * method: the denominator of the arithmetic roofline reported for the FP64
+ * split step).  Runs 8 independent FMA chains per thread on 8 CTAs of 256
+ * threads per SM, times the best of 3 launches after a warm-up with CUDA
+ * events on cuda_stream (NULL: legacy default) and writes 2 x FMAs per second
+ * to *flops_per_s, for FP64 (f64 != 0) or FP32.  Synchronous; allocates and
+ * frees one word of device memory.  SOP_EINVAL for a null output, SOP_ECUDA
+ * for a CUDA error. */
+int sop_fma_peak(int f64, double *flops_per_s, void *cuda_stream);
+
 /* Norm without any device allocation.  Not part of the paper's method (it
  * has no counterpart there); it serves callers that may not allocate device
  * memory: programs whose own pool allocator owns all of HBM and forbids
@@ -205,7 +257,9 @@ int64_t sop_launch_counter(sop_plan plan);
  * but all calls share the array: calls that may overlap on the GPU (unordered
  * streams or several host threads) race and must be serialised.  The first
  * call on each device looks up the array's device address (with that device
- * current); make that first call before any stream capture.  Returns
+ * current) and keeps it for the life of the process; make that first call
+ * before any stream capture.  Resetting a device (cudaDeviceReset) after that
+ * first call is not supported: the kept address would then be stale.  Returns
  * SOP_EINVAL for null or misaligned pointers, a bad dtype or n_values < 0. */
 int sop_norm_noalloc(const void *psi_dev, int64_t n_values, int dtype, double scale, double *out_dev,
                      void *cuda_stream);

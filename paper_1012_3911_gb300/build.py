@@ -31,6 +31,12 @@ UNITS = [
     ("pass_f64_strided", "sop_pass_inst.cu", ["-DSOP_REAL=double", "-DSOP_CONTIG=0"]),
     ("fso1d_f32", "sop_1d_inst.cu", ["-DSOP_REAL=float", "-DSOP_IS_DOUBLE=0"]),
     ("fso1d_f64", "sop_1d_inst.cu", ["-DSOP_REAL=double", "-DSOP_IS_DOUBLE=1"]),
+] + [
+    (f"pass_var{v}_f32_{'contig' if c else 'strided'}", "sop_pass_var.cu",
+     ["-DSOP_REAL=float", f"-DSOP_CONTIG={c}", f"-DSOP_VAR={v}"])
+    for v in (1, 2, 3, 4, 5, 6, 7) for c in (1, 0)
+] + [
+    ("peak", "sop_peak.cu", []),
     ("tables", "sop_tables.cu", []),
     ("reduce", "sop_reduce.cu", []),
     ("api", "sop_api.cu", []),

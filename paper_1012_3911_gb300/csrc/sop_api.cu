@@ -30,6 +30,45 @@
 #include "sop.h"
 #include "sop_internal.h"
 
+namespace sop {
+
+#define SOP_VAR_DECL(K)                                                                                          \
+    cudaError_t launch_async_var_f32_contig_##K(const PassArgs &, int, const TensorMapBytes &, cudaStream_t,     \
+                                                int64_t *);                                                      \
+    cudaError_t launch_async_var_f32_strided_##K(const PassArgs &, int, const TensorMapBytes &, cudaStream_t,    \
+                                                 int64_t *);
+SOP_VAR_DECL(1)
+SOP_VAR_DECL(2)
+SOP_VAR_DECL(3)
+SOP_VAR_DECL(4)
+SOP_VAR_DECL(5)
+SOP_VAR_DECL(6)
+SOP_VAR_DECL(7)
+#undef SOP_VAR_DECL
+
+cudaError_t launch_async_variant(bool f64, bool contig, int var, const PassArgs &a, int nc, const TensorMapBytes &tmap,
+                                 cudaStream_t s, int64_t *ctr_advance) {
+    if (f64) return cudaErrorInvalidValue;
+    switch (var) {
+#define SOP_VAR_CASE(K)                                                                \
+    case K:                                                                            \
+        return contig ? launch_async_var_f32_contig_##K(a, nc, tmap, s, ctr_advance)   \
+                      : launch_async_var_f32_strided_##K(a, nc, tmap, s, ctr_advance);
+        SOP_VAR_CASE(1)
+        SOP_VAR_CASE(2)
+        SOP_VAR_CASE(3)
+        SOP_VAR_CASE(4)
+        SOP_VAR_CASE(5)
+        SOP_VAR_CASE(6)
+        SOP_VAR_CASE(7)
+#undef SOP_VAR_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace sop
+
 using namespace sop;
 using cd = std::complex<double>;
 
@@ -111,6 +150,8 @@ struct sop_plan_s {
     unsigned long long *tile_ctr = nullptr;   // tile counters of the persistent passes (one per pair)
     unsigned long long tile_base[2] = {0, 0};   // their values at the start of the next launch
     bool async_passes = true;       // persistent passes with bulk / TMA prefetch
+    int pass_var[2][2] = {{0, 0}, {0, 0}};   // launch-shape variant per axis kind (contig, strided) and nc - 1
+    uint64_t wait_ns = 0;           // limit of the passes' tile-copy waits (0: the kernels' default)
     struct MapEntry {
         void *ptr;
         int axis, nc;
@@ -329,6 +370,7 @@ int launch_pass(sop_plan p, const PassArgs &a0, int nc, const char *what) {
     if (p->async_passes) {
         PassArgs a = a0;
         a.errflag = p->errflag;
+        a.wait_ns = p->wait_ns;
         a.tile_ctr = p->tile_ctr;
         a.stw = p->stw[a.axis][nc - 1];
         a.tile_base[0] = p->tile_base[0];
@@ -342,9 +384,17 @@ int launch_pass(sop_plan p, const PassArgs &a0, int nc, const char *what) {
                 int rc = tensor_map(p, a.psi, a.axis, nc, &tm);
                 if (rc) return rc;
             }
-            cudaError_t e;
+            cudaError_t e = cudaErrorInvalidValue;
             int64_t adv = 0;
-            if (p->f64)
+            const int var = p->pass_var[contig ? 0 : 1][nc - 1];
+            if (var > 0 && var < kPassVariants) {
+                e = launch_async_variant(p->f64, contig, var, a, nc, tm, p->stream, &adv);
+                if (e == cudaErrorInvalidValue) cudaGetLastError();   // no such variant for the size
+            }
+            if (e == cudaSuccess) {
+            } else if (e != cudaErrorInvalidValue) {
+                return cuda_fail(e, what);
+            } else if (p->f64)
                 e = contig ? launch_async_f64_contig(a, nc, tm, p->stream, &adv)
                            : launch_async_f64_strided(a, nc, tm, p->stream, &adv);
             else
@@ -1038,6 +1088,18 @@ int sop_plan_create(sop_plan *out, int ndim, const int64_t *dims, const double *
     p->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     p->csz = p->f64 ? 16 : 8;
     {
+        // "C,S": launch-shape variants of the contiguous and strided passes
+        // (both component counts) instead of the default shape
+        const char *env = std::getenv("SOP_PASS_SHAPE");
+        int vc = 0, vs = 0;
+        if (env && std::sscanf(env, "%d,%d", &vc, &vs) == 2 && vc >= 0 && vc < kPassVariants && vs >= 0 &&
+            vs < kPassVariants)
+            for (int nc = 0; nc < 2; ++nc) {
+                p->pass_var[0][nc] = vc;
+                p->pass_var[1][nc] = vs;
+            }
+    }
+    {
         const char *env = std::getenv("SOP_PASSES");   // "sync": one-shot passes (for comparisons)
         p->async_passes = !(env && std::string(env) == "sync");
     }
@@ -1120,6 +1182,7 @@ int sop_plan_create(sop_plan *out, int ndim, const int64_t *dims, const double *
                 p->launches++;
             }
         }
+
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -1292,6 +1355,104 @@ int sop_profile_read(sop_plan p, double *ms, int64_t *launches, int max_classes)
 }
 
 int64_t sop_launch_counter(sop_plan p) { return p ? p->launches : 0; }
+
+int sop_set_wait_limit(sop_plan p, uint64_t wait_ns) {
+    if (!p) return fail(SOP_EINVAL, "sop_set_wait_limit: null plan");
+    p->wait_ns = wait_ns;
+    return SOP_OK;
+}
+
+int sop_set_pass_shape(sop_plan p, int axis_kind, int shape) {
+    if (!p) return fail(SOP_EINVAL, "sop_set_pass_shape: null plan");
+    if (axis_kind != 0 && axis_kind != 1) return fail(SOP_EINVAL, "sop_set_pass_shape: axis_kind must be 0 or 1");
+    if (shape < 0 || shape >= kPassVariants) return fail(SOP_EINVAL, "sop_set_pass_shape: shape out of range");
+    p->pass_var[axis_kind][0] = p->pass_var[axis_kind][1] = shape;
+    return SOP_OK;
+}
+
+int sop_autotune(sop_plan p, double dt, int trial_steps, int *chosen) {
+    if (!p) return fail(SOP_EINVAL, "sop_autotune: null plan");
+    if (!p->psi) return fail(SOP_ESTATE, "sop_autotune: no state bound");
+    if (!is_finite(dt)) return fail(SOP_EINVAL, "sop_autotune: dt is not finite");
+    if (trial_steps <= 0) trial_steps = 16;
+    if (chosen) chosen[0] = chosen[1] = 0;
+    if (p->ndim == 1 || !p->async_passes) return SOP_OK;   // no pencil passes to shape
+    static_assert(SOP_PASS_SHAPES == kPassVariants, "shape count");
+    // per-process cache: lattice shape, components, dtype, device -> shapes
+    static std::mutex mu;
+    static std::map<std::vector<int64_t>, std::pair<int, int>> cache;
+    const std::vector<int64_t> key = {p->device, p->ndim, p->dims[0], p->dims[1], p->dims[2], p->comps, p->f64 ? 1 : 0};
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            p->pass_var[0][0] = p->pass_var[0][1] = it->second.first;
+            p->pass_var[1][0] = p->pass_var[1][1] = it->second.second;
+            if (chosen) {
+                chosen[0] = it->second.first;
+                chosen[1] = it->second.second;
+            }
+            return SOP_OK;
+        }
+    }
+    const size_t bytes = (size_t)p->npts * p->comps * p->csz;
+    int rc = SOP_OK;
+    if (!p->scratch) rc = dalloc(&p->scratch, bytes, "autotune scratch");
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(p->scratch, p->psi, bytes, cudaMemcpyDeviceToDevice, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(D2D)");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    void *const saved_psi = p->psi;
+    const int saved_prof = p->prof_every;
+    p->psi = p->scratch;
+    p->prof_every = 0;
+    int best[2] = {0, 0};
+    for (int kind = 0; kind < 2 && !rc; ++kind) {
+        float best_ms = 0.f;
+        for (int v = 0; v < kPassVariants && !rc; ++v) {
+            p->pass_var[kind][0] = p->pass_var[kind][1] = v;
+            rc = step_impl(p, 2, dt, nullptr);   // warm-up (tables, tensor maps, attributes)
+            if (rc) break;
+            cudaEventRecord(e0, p->stream);
+            rc = step_impl(p, trial_steps, dt, nullptr);
+            if (rc) break;
+            cudaEventRecord(e1, p->stream);
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+                rc = cuda_fail(e, "cudaEventSynchronize");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (v == 0 || ms < best_ms) {
+                best_ms = ms;
+                best[kind] = v;
+            }
+        }
+        p->pass_var[kind][0] = p->pass_var[kind][1] = best[kind];
+    }
+    p->psi = saved_psi;
+    p->prof_every = saved_prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!rc) rc = check_errflag(p);
+    if (rc) {
+        p->pass_var[0][0] = p->pass_var[0][1] = p->pass_var[1][0] = p->pass_var[1][1] = 0;
+        return rc;
+    }
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        cache[key] = {best[0], best[1]};
+    }
+    if (chosen) {
+        chosen[0] = best[0];
+        chosen[1] = best[1];
+    }
+    return SOP_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Batched propagation: independent 2D Schroedinger lattices of uneven sizes

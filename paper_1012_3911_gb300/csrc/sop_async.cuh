@@ -138,15 +138,75 @@ __host__ __device__ constexpr int largest_divisor_le(int n, int cap) {
 // Geometry
 // ---------------------------------------------------------------------------
 
-template <typename Real, int N, int NC, bool CONTIG> struct AsyncCfg {
-    using G = Geometry<N, NC>;
+// Launch-shape variants of the persistent pass (the autotuner picks one per
+// pass-axis size, component count and axis kind; 0 is the default shape):
+//   WP1   : contiguous axis, one pencil group of ~128 threads per CTA instead of ~256
+//   NBUF  : 1 = one tile buffer (the next tile is fetched once the current one
+//           no longer needs it; other CTAs on the SM cover the wait), 2 = two
+//           (prefetch of the next tile while this one is transformed), 0 = the
+//           default rule
+//   VPRE  : the per-point phase values of the real-space factor are fetched
+//           into registers before the tile is waited for (else just before use)
+//   L1TAB : stage twiddles and the pass-axis factor row are read through L1
+//           instead of being copied into shared memory
+//   REGS  : register budget per thread that sets the resident CTAs per SM
+//   E     : values per thread (0: the size's default, 16 for a power of two)
+//   LATE  : stage twiddles fetched after each exchange instead of before it
+//   AXL1  : only the pass-axis factor row is read through L1
+//   CT    : threads per CTA on the contiguous axis (0: 128 with WP1, else 256)
+template <int VAR> struct PassPolicy;
+struct PolBase {
+    static constexpr bool LATE = false, AXL1 = false;
+    static constexpr int E = 0, CT = 0;
+};
+template <> struct PassPolicy<0> : PolBase {
+    static constexpr bool WP1 = false, VPRE = true, L1TAB = false;
+    static constexpr int NBUF = 0, REGS = 104;
+};
+template <> struct PassPolicy<1> : PolBase {
+    static constexpr bool WP1 = true, VPRE = false, L1TAB = false;
+    static constexpr int NBUF = 1, REGS = 80;
+};
+template <> struct PassPolicy<2> : PolBase {
+    static constexpr bool WP1 = true, VPRE = false, L1TAB = true;
+    static constexpr int NBUF = 1, REGS = 64;
+};
+template <> struct PassPolicy<3> : PolBase {
+    static constexpr bool WP1 = true, VPRE = false, L1TAB = true;
+    static constexpr int NBUF = 2, REGS = 64;
+};
+template <> struct PassPolicy<4> : PolBase {
+    static constexpr bool WP1 = true, VPRE = false, L1TAB = true;
+    static constexpr int NBUF = 1, REGS = 72;
+};
+// one pencil group per CTA with the phase values prefetched (as variant 0)
+template <> struct PassPolicy<5> : PolBase {
+    static constexpr bool WP1 = true, VPRE = true, L1TAB = false;
+    static constexpr int NBUF = 1, REGS = 112;
+};
+// stage twiddles in shared memory, the pass-axis row through L1
+template <> struct PassPolicy<6> : PolBase {
+    static constexpr bool WP1 = true, VPRE = false, L1TAB = false, AXL1 = true;
+    static constexpr int NBUF = 2, REGS = 80;
+};
+template <> struct PassPolicy<7> : PolBase {
+    static constexpr bool WP1 = true, VPRE = false, L1TAB = false, AXL1 = true;
+    static constexpr int NBUF = 1, REGS = 80;
+};
+static_assert(kPassVariants == 8, "one PassPolicy per variant");
+
+template <typename Real, int N, int NC, bool CONTIG, int VAR = 0> struct AsyncCfg {
+    using Pol = PassPolicy<VAR>;
+    // 32 values per thread only where the size's default is 16
+    static constexpr int EV = (Pol::E > 0 && Geometry<N, NC>::E == 16 && N >= 512) ? Pol::E : 0;
+    using G = Geometry<N, NC, EV>;
     using C = cplx_t<Real>;
     static constexpr int E = G::E;
     static constexpr int T = G::T;
     static constexpr int CSZ = 2 * (int)sizeof(Real);
     static constexpr int PITCH = ((N + (N >> G::LR)) + 1) & ~1;   // even: rows stay 16-byte aligned
     static constexpr int wp_contig() {
-        int w = 256 / T;
+        int w = (Pol::CT > 0 ? Pol::CT : (Pol::WP1 ? 128 : 256)) / T;
         return w < 1 ? 1 : w;
     }
     static constexpr int wp_strided() {
@@ -190,8 +250,9 @@ template <typename Real, int N, int NC, bool CONTIG> struct AsyncCfg {
     // (Measured on GB300: 2048^2 c128 split steps 1394 -> 1354 us; for
     // complex64 the second buffer is worth more than the extra CTA.)
     static constexpr int ctas_smem(size_t bytes) { return (int)((228 * 1024) / (bytes + 1024)); }
-    static constexpr bool SINGLE = SOP_SINGLE_BUFFER != 0 && !CONTIG && CSZ == 16 && NC == 1 &&
-                                   ctas_smem(128 + BUF + TWZ + AXT) > ctas_smem(128 + 2 * BUF + TWZ + AXT);
+    static constexpr bool SINGLE = Pol::NBUF == 1 ||
+                                   (Pol::NBUF == 0 && SOP_SINGLE_BUFFER != 0 && !CONTIG && CSZ == 16 && NC == 1 &&
+                                    ctas_smem(128 + BUF + TWZ + AXT) > ctas_smem(128 + 2 * BUF + TWZ + AXT));
     static constexpr int NBUF = SINGLE ? 1 : 2;
     static constexpr size_t OFF_BUF = 128, OFF_TWZ = OFF_BUF + NBUF * BUF, OFF_AXT = OFF_TWZ + TWZ;
     // Lean layout: the stage twiddles are read from global memory through L1
@@ -201,14 +262,15 @@ template <typename Real, int N, int NC, bool CONTIG> struct AsyncCfg {
     // the extra CTA does not pay for the L1 reads of the axis row and the
     // twiddles; 2048^2 complex64 split steps took 61.0 instead of 56.2 us.)
     static constexpr int ctas_for(size_t bytes) { return (int)((228 * 1024) / (bytes + 1024)); }
-    static constexpr bool LEAN = SOP_LEAN_TABLES != 0 && CSZ == 8 && NC == 2 && !CONTIG &&
-                                 ctas_for(OFF_BUF + NBUF * BUF) > ctas_for(OFF_AXT + AXT);
-    static constexpr size_t SMEM = LEAN ? OFF_BUF + NBUF * BUF : OFF_AXT + AXT;
+    static constexpr bool LEAN = Pol::L1TAB || (SOP_LEAN_TABLES != 0 && CSZ == 8 && NC == 2 && !CONTIG &&
+                                                ctas_for(OFF_BUF + NBUF * BUF) > ctas_for(OFF_AXT + AXT));
+    static constexpr bool AXL1 = LEAN || Pol::AXL1;   // pass-axis row through L1
+    static constexpr size_t SMEM = LEAN ? OFF_BUF + NBUF * BUF : (AXL1 ? OFF_AXT : OFF_AXT + AXT);
     // buffer and mbarrier phase parity of iteration it
     __device__ __forceinline__ static int buf_of(int it) { return SINGLE ? 0 : (it & 1); }
     __device__ __forceinline__ static uint32_t par_of(int it) { return SINGLE ? (it & 1) : ((it >> 1) & 1); }
     static constexpr bool FITS = SMEM <= 227 * 1024 && THREADS <= 1024;
-    static constexpr int TWM = LEAN ? 2 : 1;   // twiddle source of the FFT (see StageTw)
+    static constexpr int TWM = (LEAN ? 2 : 1) | (Pol::LATE ? 4 : 0);   // twiddle source of the FFT (see StageTw)
     // On the contiguous axis a pencil is whole warps (threadIdx.y = pencil), so
     // its exchanges synchronise only its own warps (named barrier 1 + pencil).
     static constexpr bool PENCIL_BAR = CONTIG && T % 32 == 0 && WP > 1 && WP <= 15;
@@ -217,7 +279,8 @@ template <typename Real, int N, int NC, bool CONTIG> struct AsyncCfg {
     static constexpr int minb() {
         int b = (int)((227 * 1024) / (SMEM > 0 ? SMEM : 1));
         const int bt = 2048 / THREADS;
-        const int br = 65536 / (THREADS * (LEAN ? 64 : 104));   // registers per thread to leave
+        const int regs = VAR == 0 ? (LEAN ? 64 : 104) : Pol::REGS;
+        const int br = 65536 / (THREADS * regs);   // registers per thread to leave
         if (bt < b) b = bt;
         if (br < b) b = br;
         if (b > 8) b = 8;
@@ -233,11 +296,12 @@ template <typename Real, int N, int NC, bool CONTIG> struct AsyncCfg {
 // MULTI: the tiles belong to several lattices (a.inst, one component each)
 // that share the pass-axis size N; each tile takes its lattice's state,
 // tables, geometry and tensor map from the instance descriptor.
-template <typename Real, int N, int NC, bool CONTIG, bool MULTI>
-__global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncCfg<Real, N, NC, CONTIG>::MINB)
+template <typename Real, int N, int NC, bool CONTIG, bool MULTI, int VAR = 0>
+__global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, AsyncCfg<Real, N, NC, CONTIG, VAR>::MINB)
     pass_kernel_async(const __grid_constant__ PassArgs a, const __grid_constant__ CUtensorMap tmap) {
     static_assert(!MULTI || NC == 1, "multi-instance passes have one component");
-    using Cfg = AsyncCfg<Real, N, NC, CONTIG>;
+    using Cfg = AsyncCfg<Real, N, NC, CONTIG, VAR>;
+    constexpr bool VPRE = Cfg::Pol::VPRE;
     using C = cplx_t<Real>;
     using Ph = Phase<Real>;
     constexpr int E = Cfg::E, T = Cfg::T, WP = Cfg::WP, CSZ = Cfg::CSZ;
@@ -269,9 +333,15 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
     griddep_launch_dependents();
     // Tiles are claimed one at a time (thread 0), so SMs that run ahead take
     // more of them whatever the placement of the CTAs.
+    // A claim below the launch's base can only follow a launch whose CTAs
+    // gave up (their claims fell short); it counts as past the last tile.
     auto claim = [&]() -> int64_t {
-        return (int64_t)(atomicAdd(a.tile_ctr + pz, 1ull) - a.tile_base[pz]);
+        const int64_t c = (int64_t)(atomicAdd(a.tile_ctr + pz, 1ull) - a.tile_base[pz]);
+        return c < 0 ? ntiles : c;
     };
+    // tile copies wait at most this long (a.wait_ns > 0 shortens it to test
+    // the error path); drains after giving up always use the full limit
+    const uint64_t wait_ns = a.wait_ns > 0 ? a.wait_ns : kWaitLimitNs;
 
     if (tid == 0) {
         mbar_init(bar0, 1);
@@ -442,11 +512,15 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
 
     // axis table copied into shared memory (single lattice; multi-instance
     // passes read each lattice's row through L1)
-    const bool axt_smem = !Cfg::LEAN && !MULTI && axsrc != nullptr;
+    const bool axt_smem = !Cfg::AXL1 && !MULTI && axsrc != nullptr;
     // Before this point only the stage twiddles (written when the plan was
     // made) are read.  psi and the phase tables may come from the kernel
     // just before this one in the stream.
     griddep_wait();
+    // An earlier pass of this stream gave up waiting (its tiles are
+    // unfinished and the tile counters are behind): do nothing until the
+    // host, which reports SOP_ETIMEOUT, has reset them.
+    if (*reinterpret_cast<volatile int *>(a.errflag) != 0) return;
     // Thread 0 claims one tile ahead: the claim for the tile after the
     // current one is made when the current one is issued, so the latency of
     // the atomic is hidden behind a whole tile.  Claims stop after the first
@@ -468,7 +542,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
     int64_t tile = s_tile[0];
     if (tile >= ntiles) return;   // nothing claimed, nothing in flight
     if (axt_smem) {
-        const bool okx = mbar_wait_bounded(barx, 0, kWaitLimitNs);
+        const bool okx = mbar_wait_bounded(barx, 0, wait_ns);
         if (!__syncthreads_and(okx)) {
             give_up(0, true, false, true);
             return;
@@ -501,7 +575,10 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
             publish_next();
             issue_next();
         };
-        if (CONTIG && tid == 0) claim_next();
+        if (CONTIG && tid == 0) {
+            if constexpr (Cfg::SINGLE) publish_next();   // issued once the buffer is free
+            else claim_next();
+        }
 
         int64_t ltile = tile;
         const InstDesc *dp = nullptr;
@@ -548,21 +625,27 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
             for (int c = 0; c < NC; ++c) coff[c] = comp_index(c, bidx) * pv_i64(dp, 6);
         }
 
-        // Per-point phase values of this pencil, fetched now and used after
-        // the first transform (bypassing L1).
-        C vpre[E];
-        if (want_v) {
-            const C *vt = pv_vtab(dp) + base;
+        // Per-point phase values of this pencil (bypassing L1): fetched now
+        // and used after the first transform (VPRE), or loaded where used.
+        const C *const vt = want_v ? pv_vtab(dp) + base : nullptr;
+        C vpre[VPRE ? E : 1];
+        if constexpr (VPRE) {
+            if (want_v) {
 #pragma unroll
-            for (int m = 0; m < E; ++m) vpre[m] = ld_stream(vt + (t + T * m));
-        } else {
+                for (int m = 0; m < E; ++m) vpre[m] = ld_stream(vt + (t + T * m));
+            } else {
 #pragma unroll
-            for (int m = 0; m < E; ++m) vpre[m] = Ph::one();
+                for (int m = 0; m < E; ++m) vpre[m] = Ph::one();
+            }
         }
+        auto vph = [&](int m) -> C {
+            if constexpr (VPRE) return vpre[m];
+            else return want_v ? ld_stream(vt + (t + T * m)) : Ph::one();
+        };
 
-        bool ok = mbar_wait_bounded(b ? bar1 : bar0, Cfg::par_of(it), kWaitLimitNs);
+        bool ok = mbar_wait_bounded(b ? bar1 : bar0, Cfg::par_of(it), wait_ns);
         if (!__syncthreads_and(ok)) {
-            give_up(it, true, CONTIG && has_next, false);
+            give_up(it, true, CONTIG && !Cfg::SINGLE && has_next, false);
             return;
         }
 
@@ -605,7 +688,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
                 const C *tab[3];
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax) tab[ax] = pv_row(dp, ax);
-                const C *const axsrc_t = (MULTI || Cfg::LEAN) ? pv_row(dp, a.axis) : axsrc;
+                const C *const axsrc_t = (MULTI || Cfg::AXL1) ? pv_row(dp, a.axis) : axsrc;
                 const bool has_axt = axsrc_t != nullptr;
                 C g = Ph::one();
                 bool g_set = false;
@@ -624,7 +707,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
                     shi = Real(a.scale_hi);
                     slo = Real(a.scale_lo);
                 }
-                auto axis_at = [&](int i) -> C { return (Cfg::LEAN || MULTI) ? ldg_c(axsrc_t + i) : axt[i]; };
+                auto axis_at = [&](int i) -> C { return (Cfg::AXL1 || MULTI) ? ldg_c(axsrc_t + i) : axt[i]; };
                 // f = [V phase] [axis factor] [g], then psi <- psi (1 + f) [* 1/N].
                 auto loop = [&](auto hv_c, auto axt_c, auto g_c, auto scale_c) {
                     constexpr bool HV = decltype(hv_c)::value, AX = decltype(axt_c)::value;
@@ -632,7 +715,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
                     constexpr int SC = decltype(scale_c)::value;   // 0: none, 1: hi only, 2: hi + lo
 #pragma unroll
                     for (int m = 0; m < E; ++m) {
-                        C f = HV ? vpre[m] : (AX ? axis_at(t + T * m) : (GG ? g : Ph::one()));
+                        C f = HV ? vph(m) : (AX ? axis_at(t + T * m) : (GG ? g : Ph::one()));
                         if constexpr (HV && AX) f = Ph::combine(axis_at(t + T * m), f);
                         if constexpr (GG && (HV || AX)) f = Ph::combine(f, g);
                         C r = Ph::apply(v[0][m], f);
@@ -661,7 +744,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
                         C f = g;
                         if (has_axt) f = Ph::combine(axis_at(t + T * m), f);
                         if (op_v) {
-                            f = Ph::combine(vpre[m], f);
+                            f = Ph::combine(vph(m), f);
                             v[0][m] = Ph::apply(v[0][m], f);
                         } else {
                             v[0][m] = scale2(Ph::apply(v[0][m], f), shi, slo);
@@ -680,8 +763,9 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
                     C u0 = cadd(cmul(m00, v[0][m]), cmul(m01, v[1][m]));
                     C u1 = cadd(cmul(m10, v[0][m]), cmul(m11, v[1][m]));
                     if (want_v) {
-                        u0 = Ph::apply(u0, vpre[m]);
-                        u1 = Ph::apply(u1, vpre[m]);
+                        const C vm = vph(m);
+                        u0 = Ph::apply(u0, vm);
+                        u1 = Ph::apply(u1, vm);
                     }
                     v[0][m] = u0;
                     v[1][m] = u1;
@@ -697,6 +781,13 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
         }
 
         if constexpr (CONTIG) {
+            if constexpr (Cfg::SINGLE) {
+                // Every read of the only buffer is done: fetch the next tile
+                // into it while this one is stored from registers.  s_tile of
+                // the next iteration was published before this barrier.
+                __syncthreads();
+                if (tid == 0) issue_next();
+            }
             if (active) {
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
@@ -705,7 +796,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG>::THREADS, AsyncC
                     for (int m = 0; m < E; ++m) st_stream(dst + T * m, v[c][m]);
                 }
             }
-            __syncthreads();   // the tile buffer is free again; s_tile of the next iteration is set
+            if constexpr (!Cfg::SINGLE) __syncthreads();   // the tile buffer is free again; s_tile is set
         } else {
             // Back into the landing layout, then one TMA store per box (clipped at
             // the lattice edge, so inactive pencils are never written).
@@ -756,9 +847,9 @@ int stage_table_t(void *out, const void *tw, cudaStream_t s) {
 cudaError_t ensure_smem_attr(const void *kern, int bytes);
 cudaError_t persistent_grid(const void *kern, int threads, size_t smem, int *blocks_per_sm, int *sms);
 
-template <typename Real, int N, int NC, bool CONTIG>
+template <typename Real, int N, int NC, bool CONTIG, int VAR = 0>
 cudaError_t launch_async_t(const PassArgs &a0, const TensorMapBytes &tm, cudaStream_t s, int64_t *ctr_advance) {
-    using Cfg = AsyncCfg<Real, N, NC, CONTIG>;
+    using Cfg = AsyncCfg<Real, N, NC, CONTIG, VAR>;
     if constexpr (!Cfg::FITS) {
         return cudaErrorInvalidValue;
     } else {
@@ -779,9 +870,9 @@ cudaError_t launch_async_t(const PassArgs &a0, const TensorMapBytes &tm, cudaStr
         }
         *ctr_advance = 0;
         if (a.n_tiles <= 0) return cudaSuccess;
-        auto kern = pass_kernel_async<Real, N, NC, CONTIG, false>;
+        auto kern = pass_kernel_async<Real, N, NC, CONTIG, false, VAR>;
         if constexpr (NC == 1)
-            if (multi) kern = pass_kernel_async<Real, N, NC, CONTIG, true>;
+            if (multi) kern = pass_kernel_async<Real, N, NC, CONTIG, true, VAR>;
         cudaError_t e = ensure_smem_attr(reinterpret_cast<const void *>(kern), (int)Cfg::SMEM);
         if (e != cudaSuccess) return e;
         int per_sm = 0, sms = 0;

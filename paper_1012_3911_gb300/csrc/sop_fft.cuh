@@ -170,6 +170,56 @@ template <int J, typename C> __device__ __forceinline__ C rot48(C x) {
 // a * exp(-2 pi i J / 16) for the radix-2^k butterflies.
 template <int J, typename C> __device__ __forceinline__ C w16(C a) { return rot48<3 * J>(a); }
 
+// sin x and cos x for |x| <= pi/2 in constant expressions (Taylor series
+// summed to 16 terms; the next term is below 1e-25 there).
+__host__ __device__ constexpr double ct_sin(double x) {
+    double term = x, sum = x;
+    for (int k = 1; k < 16; ++k) {
+        term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double ct_cos(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 16; ++k) {
+        term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+        sum += term;
+    }
+    return sum;
+}
+constexpr double kPiD = 3.14159265358979323846264338327950288;
+
+// x * exp(-2 pi i J / O) for any order O that is a multiple of 4: quarter
+// turns, then the remaining angle phi = 2 pi j / O < pi/2 as the three
+// shears of rot48 (determinant 1 whatever the rounding of tan(phi/2) and
+// sin(phi)).  Orders dividing 48 use rot48's constants.
+template <int J, int O, typename C> __device__ __forceinline__ C rotq(C x) {
+    if constexpr (48 % O == 0) {
+        return rot48<(((J % O) + O) % O) * (48 / O)>(x);
+    } else {
+        static_assert(O % 4 == 0, "root order");
+        using R = decltype(x.x);
+        constexpr int jj = ((J % O) + O) % O;
+        constexpr int q = (4 * jj) / O, j = jj - q * (O / 4);
+        C y = x;
+        if constexpr (q == 1) y = mul_mi(x);
+        else if constexpr (q == 2) y = mk<C>(-x.x, -x.y);
+        else if constexpr (q == 3) y = mul_pi(x);
+        if constexpr (j == 0) {
+            return y;
+        } else {
+            constexpr double half = kPiD * j / O;
+            constexpr R t = R(ct_sin(half) / ct_cos(half));
+            constexpr R sn = R(ct_sin(2.0 * half));
+            R a = fmar(t, y.y, y.x);
+            const R b = fmar(-sn, a, y.y);
+            a = fmar(t, b, a);
+            return mk<C>(a, b);
+        }
+    }
+}
+
 // Compile-time loop: f(std::integral_constant<int, I>) for I in [B, E).
 template <int B, int E, typename F> __device__ __forceinline__ void sfor(F &&f) {
     if constexpr (B < E) {
@@ -182,7 +232,7 @@ template <int R> struct Dft;
 
 template <int R, int K, typename C> __device__ __forceinline__ void dit_combine(C *x, const C *e, const C *o) {
     if constexpr (K < R / 2) {
-        const C t = w16<K * 16 / R>(o[K]);
+        const C t = rotq<K, R>(o[K]);
         x[K] = cadd(e[K], t);
         x[K + R / 2] = csub(e[K], t);
         dit_combine<R, K + 1>(x, e, o);
@@ -209,7 +259,7 @@ template <int R> struct Dft {
             x[1] = mk<C>(m.x + u.y, m.y - u.x);  // m - i u
             x[2] = mk<C>(m.x - u.y, m.y + u.x);  // m + i u
         } else {
-            static_assert(R == 4 || R == 8 || R == 16, "radix");
+            static_assert(R == 4 || R == 8 || R == 16 || R == 32 || R == 64, "radix");
             constexpr int H = R / 2;
             C e[H], o[H];
 #pragma unroll
@@ -272,8 +322,9 @@ __host__ __device__ constexpr int ilog2c(int x) {
 
 // Elements per thread: 16 (scalar) or 8 (two coupled components) for powers
 // of two; for n = 3*2^k, 8*3 or 4*3.  Small sizes use one thread per pencil.
-template <int N, int NC> struct Geometry {
+template <int N, int NC, int EOV = 0> struct Geometry {
     static constexpr int E_calc() {
+        if (EOV > 0) return EOV;   // an explicit choice (launch-shape variants)
         if (N % 3 == 0) {
             int base = (NC == 1) ? 8 : 4;
             const int p2 = N / 3;
@@ -388,9 +439,11 @@ template <typename C, int N, int E, int S> struct StageTw {
     static constexpr int NS = (S < P.S) ? P.NS[S] : 1;
     static constexpr int T = N / E;
     C z[R > 1 ? R - 1 : 1];
-    // Twiddle source TWM: 0 = the full W_n table in global memory; 1 = this
-    // size's per-stage table (see StageTable) in shared memory; 2 = the same
-    // per-stage table in global memory, read through L1.
+    // Twiddle source TWM & 3: 0 = the full W_n table in global memory; 1 =
+    // this size's per-stage table (see StageTable) in shared memory; 2 = the
+    // same per-stage table in global memory, read through L1.  TWM & 4: the
+    // next stage's twiddles are fetched after the exchange instead of before
+    // it (fewer registers live across the exchange).
     template <int TWM>
     __device__ __forceinline__ void load(const C *__restrict__ tab, int t);
 };
@@ -426,12 +479,12 @@ template <int TWM>
 __device__ __forceinline__ void StageTw<C, N, E, S>::load(const C *__restrict__ tab, int t) {
     if constexpr (S > 0 && S < P.S) {
         static_assert(NS % T == 0 || T % NS == 0, "stage twiddles must split");
-        if constexpr (TWM != 0) {
+        if constexpr ((TWM & 3) != 0) {
             constexpr int KS = StageTable<C, N, E>::ks(S), OFF = StageTable<C, N, E>::off(S);
             const int k = t % KS;
 #pragma unroll
             for (int r = 1; r < R; ++r)
-                z[r - 1] = TWM == 1 ? tab[OFF + (r - 1) * KS + k] : ldg_c(tab + OFF + (r - 1) * KS + k);
+                z[r - 1] = (TWM & 3) == 1 ? tab[OFF + (r - 1) * KS + k] : ldg_c(tab + OFF + (r - 1) * KS + k);
         } else {
             const int k = t % NS;
 #pragma unroll
@@ -470,8 +523,7 @@ __device__ __forceinline__ void fft_stage(C (&v)[E], const Lay &lay, int t, cons
                 if constexpr (NS > T) {
                     constexpr int M = NS / T;           // distinct j mod Ns per thread
                     constexpr int O = NS * R / T;       // order of the extra root
-                    static_assert(48 % O == 0, "root order");
-                    x[r] = rot48<((q % M) * r % O) * (48 / O)>(x[r]);
+                    x[r] = rotq<((q % M) * r) % O, O>(x[r]);
                 }
             });
         }
@@ -509,7 +561,7 @@ __device__ __forceinline__ void fft_forward_from(C (&v)[NC][E], const Lay (&lay)
         if constexpr (S + 1 < P.S) {
             constexpr int T = N / E;
             StageTw<C, N, E, S + 1> nxt;
-            nxt.template load<SMEM>(tab, t);
+            if constexpr ((SMEM & 4) == 0) nxt.template load<SMEM>(tab, t);
             bar.sync();
             if constexpr (LayFast<Lay>::value && read_split_ok<N, E, LayFast<Lay>::LR>()) {
 #pragma unroll
@@ -527,6 +579,7 @@ __device__ __forceinline__ void fft_forward_from(C (&v)[NC][E], const Lay (&lay)
                     for (int m = 0; m < E; ++m) v[c][m] = lay[c].ld(t + T * m);
             }
             bar.sync();
+            if constexpr ((SMEM & 4) != 0) nxt.template load<SMEM>(tab, t);
             fft_forward_from<C, N, E, NC, S + 1, SMEM>(v, lay, t, tab, nxt, bar);
         }
     }

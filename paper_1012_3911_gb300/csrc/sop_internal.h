@@ -48,6 +48,7 @@ struct PassArgs {
     int pair_comp[2][2];     // component indices of each pair
     // Persistent asynchronous passes (filled by the launcher)
     int *errflag;            // device word; bit 1 set when a bounded wait gave up
+    uint64_t wait_ns;        // limit of the tile-copy waits (0: kWaitLimitNs)
     // Dynamic tile scheduling: CTAs claim tiles with atomicAdd on
     // tile_ctr[pz] (pz: component pair); claim - tile_base[pz] is the tile
     // index.  A launch advances each counter it uses by n_tiles + gridDim.x
@@ -148,6 +149,12 @@ cudaError_t launch_async_f64_contig(const PassArgs &a, int nc, const TensorMapBy
                                  int64_t *ctr_advance);
 cudaError_t launch_async_f64_strided(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s,
                                  int64_t *ctr_advance);
+// Launch-shape variants 1 .. kPassVariants - 1 of the persistent pass
+// (sop_pass_var.cu, complex64 only); cudaErrorInvalidValue for a size, dtype
+// or variant without a kernel.
+constexpr int kPassVariants = 8;
+cudaError_t launch_async_variant(bool f64, bool contig, int var, const PassArgs &a, int nc, const TensorMapBytes &tmap,
+                                 cudaStream_t s, int64_t *ctr_advance);
 // Adjoint-gradient reductions (sop_adjoint.cu).  launch_inner writes 8
 // doubles to out: dV (<a|b>, <a|X_0|b>, <a|X_1|b>, <a|X_2|b>) as re, im
 // pairs (axes beyond ndim are zero); partial holds inner_partials() doubles.

@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(kThreads) k_final(const double *partials, int 
 // Device address of the scratch array on the current device.  Host code must
 // not pass the symbol itself to a kernel (on the host it names a host-side
 // stand-in); the address is looked up once per device with that device
-// current and cached.
+// current and cached for the life of the process (a cudaDeviceReset after
+// the first call would leave it stale; the header says so).
 int scratch_address(double **out) {
     static std::mutex mu;
     static double *addr[kMaxDevices] = {};

@@ -203,15 +203,77 @@ def sop_launch_counter(plan: int) -> int:
     return int(load().sop_launch_counter(plan))
 
 
+SOP_PASS_SHAPES = 8
+
+
+def sop_autotune(plan: int, dt: float, trial_steps: int = 16):
+    """Time every launch shape of the plan's pencil passes on a scratch copy
+    of the state and keep the fastest; returns [contiguous, strided] shape."""
+    lib = load()
+    fn = lib.sop_autotune
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    fn.restype = ctypes.c_int
+    chosen = (ctypes.c_int * 2)()
+    _check(fn(plan, float(dt), int(trial_steps), chosen))
+    return [int(chosen[0]), int(chosen[1])]
+
+
+def sop_set_pass_shape(plan: int, axis_kind: int, shape: int) -> None:
+    """Force launch shape ``shape`` for the contiguous (0) or strided (1) passes."""
+    lib = load()
+    fn = lib.sop_set_pass_shape
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    fn.restype = ctypes.c_int
+    _check(fn(plan, int(axis_kind), int(shape)))
+
+
+def sop_fma_peak(f64: bool = True, stream=None) -> float:
+    """Measured FMA throughput of the current device in flop/s (FP64 or FP32)."""
+    lib = load()
+    fn = lib.sop_fma_peak
+    fn.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    out = ctypes.c_double()
+    _check(fn(1 if f64 else 0, ctypes.byref(out), _stream_handle(stream)))
+    return out.value
+
+
+def sop_set_wait_limit(plan: int, wait_ns: int) -> None:
+    """Limit of the pass kernels' tile-copy waits in ns (0: the default 2 s)."""
+    lib = load()
+    fn = lib.sop_set_wait_limit
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+    fn.restype = ctypes.c_int
+    _check(fn(plan, int(wait_ns)))
+
+
+def _check_noalloc_tensors(psi, n_values: int, dtype: int, out) -> None:
+    """Reject tensors the kernel would read or write out of bounds."""
+    import torch
+    if not isinstance(psi, int):
+        want = {SOP_C64: torch.complex64, SOP_C128: torch.complex128}.get(int(dtype))
+        if not (isinstance(psi, torch.Tensor) and psi.is_cuda and psi.is_contiguous()):
+            raise ValueError("psi must be a contiguous CUDA tensor (or a raw device pointer)")
+        if want is None or psi.dtype != want:
+            raise ValueError(f"psi has dtype {psi.dtype}, which does not match dtype={dtype}")
+        if psi.numel() < int(n_values):
+            raise ValueError(f"psi holds {psi.numel()} values, fewer than n_values={n_values}")
+    if not isinstance(out, int):
+        if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64 and out.numel() >= 1):
+            raise ValueError("out must be a float64 CUDA tensor with at least one element (or a raw pointer)")
+
+
 def sop_norm_noalloc(psi, n_values: int, dtype: int, scale: float, out, stream=None) -> None:
     """Asynchronous norm without device allocation: writes scale * sum |psi|^2
     into the one-element float64 CUDA tensor ``out``.  ``psi`` is a CUDA
-    tensor or a raw device pointer holding n_values complex values."""
+    tensor or a raw device pointer holding n_values complex values; tensors
+    are checked for device, layout, dtype and size first."""
     lib = load()
     fn = lib.sop_norm_noalloc
     fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
                    ctypes.c_void_p]
     fn.restype = ctypes.c_int
+    _check_noalloc_tensors(psi, n_values, dtype, out)
     ptr = psi if isinstance(psi, int) else psi.data_ptr()
     optr = out if isinstance(out, int) else out.data_ptr()
     _check(fn(ptr, int(n_values), int(dtype), float(scale), optr, _stream_handle(stream)))
@@ -406,6 +468,14 @@ class Propagator:
 
     def step_host(self, psi_host, n_steps: int, dt: float, field=None) -> None:
         sop_step_host(self.plan, psi_host, n_steps, dt, field, self.ndim)
+
+    def autotune(self, dt: float, trial_steps: int = 16):
+        """Pick the fastest launch shape of each pass kind (results are
+        bit-identical across shapes); returns [contiguous, strided]."""
+        return sop_autotune(self.plan, dt, trial_steps)
+
+    def set_pass_shape(self, axis_kind: int, shape: int) -> None:
+        sop_set_pass_shape(self.plan, axis_kind, shape)
 
     def norm(self) -> float:
         return sop_norm(self.plan)

@@ -78,3 +78,21 @@ def test_null_arguments(lib):
     cs = (ctypes.c_double * 1)(-1.0)
     assert lib.sop_plan_create(ctypes.byref(out), 1, cd, cs, 1, 0, None, None) == sop.SOP_EINVAL
     assert lib.sop_plan_create(ctypes.byref(out), 1, cd, (ctypes.c_double * 1)(0.1), 1, 7, None, None) == sop.SOP_EINVAL
+
+
+def test_pass_shape_calls_reject_bad_arguments(lib):
+    lib.sop_set_pass_shape.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    lib.sop_autotune.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p]
+    assert lib.sop_set_pass_shape(None, 0, 0) == sop.SOP_EINVAL
+    assert lib.sop_autotune(None, 0.1, 4, None) == sop.SOP_EINVAL
+    assert sop.SOP_PASS_SHAPES == 8
+
+
+def test_noalloc_wrapper_rejects_unsafe_tensors():
+    """The Python wrapper checks tensors before the kernel could read or
+    write out of bounds (no GPU call is made for a rejected argument)."""
+    import torch
+    cpu = torch.zeros(16, dtype=torch.complex64)
+    out = torch.zeros(1, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        sop.sop_norm_noalloc(cpu, 16, sop.SOP_C64, 1.0, out)   # not a CUDA tensor

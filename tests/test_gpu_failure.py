@@ -1,0 +1,48 @@
+"""Failure detection of the persistent passes without faulting the GPU: a
+wait limit of 1 ns makes the pass kernels' tile-copy waits give up while the
+copies themselves complete normally.  The next synchronising call must report
+SOP_ETIMEOUT, and after the default limit is restored the same plan must step
+correctly again (element by element against the oracle)."""
+import numpy as np
+import pytest
+import torch
+
+import gpu_cases as gc
+from paper_1012_3911_gb300 import sop
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu(orc):
+    gc.require_gpu()
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("dims", [(512, 384), (64, 48, 96)])
+def test_bounded_wait_gives_up_then_the_plan_recovers(dtype, dims):
+    w = gc.random_workload(dims, 1, seed=31 + len(dims), n_steps=4, dt=0.01, field_scale=0.05)
+    prop = sop.Propagator(w.dims, w.spacing, 1, dtype)
+    prop.set_state(torch.from_numpy(w.psi0))
+    prop.set_potential(w.V)
+    sop.sop_set_wait_limit(prop.plan, 1)
+    status = None
+    for _ in range(5):   # a wait gives up unless every copy landed before its first poll
+        prop.step(w.n_steps, w.dt, w.field)
+        try:
+            prop.norm()
+        except sop.SopError as e:
+            status = e.status
+            break
+    assert status == sop.SOP_ETIMEOUT
+    assert "bounded wait" in sop.sop_last_error()
+    # the error word and the tile counters were cleared by that report
+    sop.sop_set_wait_limit(prop.plan, 0)
+    prop.set_state(torch.from_numpy(w.psi0))
+    prop.step(w.n_steps, w.dt, w.field)
+    assert abs(prop.norm() - gc.oracle.norm(w.psi0, w.spacing)) < 1e-4
+    out = prop.state.cpu().numpy()
+    ref = gc.run_oracle(w)
+    err = gc.relerr(out, ref)
+    prop.close()
+    assert err < (gc.TOL_F64 if dtype == "c128" else gc.TOL_F32_SHORT), err

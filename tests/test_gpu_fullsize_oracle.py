@@ -1,0 +1,88 @@
+"""Every paper-shaped configuration at its full lattice and its full step
+count against the FP64 oracle (Eq. 8 with the splits of Secs. 2.2 and 2.3):
+
+  config 2: 2D Schroedinger 2048^2, 5000 steps;
+  config 3: 3D Schroedinger 512^3, 200 steps;
+  config 4: 2D Dirac 1024^2 x 4 components, 1000 steps;
+
+each in complex128 (bar 1e-10 relative L2) and complex64 (bar 2e-4).  The
+oracle needs 6 to 45 minutes per run on the host cores, so its final states
+were computed once by ``tests/golden/make_fullsize.py`` (which calls only the
+oracle and the seeded input generators) and stored as a seeded sample of
+about 16k lattice values per configuration -- 8192 drawn uniformly over all
+components and residue classes, 8192 drawn where |psi_N|^2 lives -- with the
+oracle's norm and field-free energy of the whole final state.  The GPU runs
+the same inputs in the launch configuration the benchmark times and is
+compared element by element on those samples, and on the whole state through
+norm and energy."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import gpu_cases as gc
+from paper_1012_3911_gb300 import sop, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    gc.require_gpu()
+
+
+_W = {}
+
+
+def workload(cfg):
+    if cfg not in _W:
+        _W.clear()
+        _W[cfg] = wl.CONFIGS[cfg]()
+    return _W[cfg]
+
+
+def fixture(cfg):
+    path = os.path.join(GOLDEN, f"fullsize_config{cfg}.npz")
+    g = np.load(path)
+    w = workload(cfg)
+    # the stored values belong to these inputs (sums compared loosely: NumPy's
+    # exp and sin may round differently on another platform)
+    assert tuple(g["dims"]) == w.dims and int(g["n_steps"]) == w.n_steps and float(g["dt"]) == w.dt
+    assert abs(complex(g["psi0_sum"]) - complex(w.psi0.sum())) <= 1e-9 * abs(complex(g["psi0_sum"]))
+    assert abs(float(g["V_sum"]) - float(w.V.sum())) <= 1e-9 * abs(float(g["V_sum"]))
+    assert abs(float(g["field_sum"]) - float(np.asarray(w.field).sum())) <= 1e-9 * max(1.0, abs(float(g["field_sum"])))
+    return g
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("cfg", [2, 4, 3])
+def test_full_size_full_length_against_the_oracle(cfg, dtype):
+    g = fixture(cfg)
+    w = workload(cfg)
+    prop = sop.Propagator(w.dims, w.spacing, w.comps, dtype,
+                          params=dict(mass=w.mass, charge=w.charge, hbar=w.hbar, c=w.c))
+    prop.autotune(w.dt, 8)   # the benchmark's launch shapes
+    prop.set_state(torch.from_numpy(w.psi0))
+    prop.set_potential(w.V)
+    prop.step(w.n_steps, w.dt, w.field)
+    torch.cuda.synchronize()
+    idx = torch.from_numpy(g["idx"]).cuda()
+    got = prop.state.reshape(-1)[idx].to(torch.complex128).cpu().numpy()
+    ref = g["values"]
+    err = gc.relerr(got, ref)
+    norm = prop.norm()
+    energy = prop.energy()
+    prop.close()
+    tol = gc.TOL_F64 if dtype == "c128" else gc.TOL_F32_FULL
+    print(f"config {cfg} {dtype}: sampled relL2 {err:.3e}, norm {norm:.15f} (oracle {float(g['norm']):.15f}), "
+          f"energy {energy:.12g} (oracle {float(g['energy']):.12g})")
+    assert err < tol, err
+    if dtype == "c128":
+        assert abs(norm - float(g["norm"])) < 1e-12
+        # energy: FP64 sums of the same state in another order
+        assert abs(energy - float(g["energy"])) < 1e-10 * max(1.0, abs(float(g["energy"])))
+    else:
+        assert abs(norm - float(g["norm"])) < 2e-4

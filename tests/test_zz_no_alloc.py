@@ -50,19 +50,49 @@ def test_no_alloc_norm_matches_sop_norm_on_two_calls(dtype):
 
 
 def test_no_alloc_rejects_bad_sizes_and_pointers():
+    """The C entry point's own checks (raw pointers, so the Python wrapper's
+    tensor checks do not intercept them), then the wrapper's tensor checks."""
     import torch
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
     psi = torch.zeros(16, dtype=torch.complex64, device="cuda")
+    p, o = psi.data_ptr(), out.data_ptr()
     with pytest.raises(sop.SopError) as ei:
-        sop.sop_norm_noalloc(psi, (1 << 29) + 1, sop.SOP_C64, 1.0, out)
+        sop.sop_norm_noalloc(p, (1 << 29) + 1, sop.SOP_C64, 1.0, o)
     assert ei.value.status == sop.SOP_EUNSUPPORTED
     assert "2^29" in str(ei.value)
     with pytest.raises(sop.SopError) as ei:
-        sop.sop_norm_noalloc(psi, -1, sop.SOP_C64, 1.0, out)
+        sop.sop_norm_noalloc(p, -1, sop.SOP_C64, 1.0, o)
     assert ei.value.status == sop.SOP_EINVAL
     with pytest.raises(sop.SopError) as ei:
-        sop.sop_norm_noalloc(psi, 16, 9, 1.0, out)
+        sop.sop_norm_noalloc(p, 16, 9, 1.0, o)
     assert ei.value.status == sop.SOP_EINVAL
     sop.sop_norm_noalloc(psi, 0, sop.SOP_C64, 1.0, out)
     torch.cuda.synchronize()
     assert out.item() == 0.0
+    # tensors the kernel would overrun, or of the wrong kind, never reach it
+    with pytest.raises(ValueError):
+        sop.sop_norm_noalloc(psi, 17, sop.SOP_C64, 1.0, out)            # more values than psi holds
+    with pytest.raises(ValueError):
+        sop.sop_norm_noalloc(psi, 16, sop.SOP_C128, 1.0, out)           # dtype mismatch
+    with pytest.raises(ValueError):
+        sop.sop_norm_noalloc(psi[::2], 8, sop.SOP_C64, 1.0, out)        # not contiguous
+    with pytest.raises(ValueError):
+        sop.sop_norm_noalloc(psi, 16, sop.SOP_C64, 1.0, out.float())    # out not float64
+
+
+def test_no_alloc_call_leaves_free_device_memory_unchanged():
+    """After a first call (which may load the library's module, and with it
+    the fixed scratch array), further calls allocate nothing: the device's
+    free memory is the same before and after."""
+    import torch
+    psi = torch.ones(1 << 20, dtype=torch.complex64, device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    sop.sop_norm_noalloc(psi, psi.numel(), sop.SOP_C64, 1.0, out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        sop.sop_norm_noalloc(psi, psi.numel(), sop.SOP_C64, 1.0, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert out.item() == float(psi.numel())
