@@ -67,6 +67,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Non-blocking probe of the phase (no suspend hint): used when a short wait
+// limit must be honoured to the timer's resolution.
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -77,6 +90,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
+}
+// The same with a caller-set limit (sop_set_wait_limit): polled with the
+// non-blocking probe, so even a limit of a few ns gives up on a copy still
+// in flight (try_wait may itself suspend for longer than such a limit).
+__device__ __forceinline__ bool mbar_wait_limit(uint32_t bar, uint32_t parity, uint64_t limit_ns, bool custom) {
+    if (!custom) return mbar_wait_bounded(bar, parity, limit_ns);
+    const uint64_t t0 = global_ns();
+    while (!mbar_test_wait(bar, parity))
         if (global_ns() - t0 > limit_ns) return false;
     return true;
 }
@@ -270,7 +293,8 @@ template <typename Real, int N, int NC, bool CONTIG, int VAR = 0> struct AsyncCf
     __device__ __forceinline__ static int buf_of(int it) { return SINGLE ? 0 : (it & 1); }
     __device__ __forceinline__ static uint32_t par_of(int it) { return SINGLE ? (it & 1) : ((it >> 1) & 1); }
     static constexpr bool FITS = SMEM <= 227 * 1024 && THREADS <= 1024;
-    static constexpr int TWM = (LEAN ? 2 : 1) | (Pol::LATE ? 4 : 0);   // twiddle source of the FFT (see StageTw)
+    // twiddle source of the FFT (see StageTw) and the late write barrier (see fft_forward_from)
+    static constexpr int TWM = (LEAN ? 2 : 1) | (Pol::LATE ? 4 : 0) | 8;
     // On the contiguous axis a pencil is whole warps (threadIdx.y = pencil), so
     // its exchanges synchronise only its own warps (named barrier 1 + pencil).
     static constexpr bool PENCIL_BAR = CONTIG && T % 32 == 0 && WP > 1 && WP <= 15;
@@ -542,7 +566,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
     int64_t tile = s_tile[0];
     if (tile >= ntiles) return;   // nothing claimed, nothing in flight
     if (axt_smem) {
-        const bool okx = mbar_wait_bounded(barx, 0, wait_ns);
+        const bool okx = mbar_wait_limit(barx, 0, wait_ns, a.wait_ns > 0);
         if (!__syncthreads_and(okx)) {
             give_up(0, true, false, true);
             return;
@@ -643,7 +667,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
             else return want_v ? ld_stream(vt + (t + T * m)) : Ph::one();
         };
 
-        bool ok = mbar_wait_bounded(b ? bar1 : bar0, Cfg::par_of(it), wait_ns);
+        bool ok = mbar_wait_limit(b ? bar1 : bar0, Cfg::par_of(it), wait_ns, a.wait_ns > 0);
         if (!__syncthreads_and(ok)) {
             give_up(it, true, CONTIG && !Cfg::SINGLE && has_next, false);
             return;
@@ -671,7 +695,8 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
                 for (int m = 0; m < E; ++m) v[c][m] = col[(t + T * m) * WP];
             }
         }
-        pbar.sync();   // the landing rows become exchange rows
+        // the landing rows become exchange rows: a transform's first writes
+        // wait at its late barrier until every landing read is done
 
         if (a.pre != 0) fft_dir<C, N, E, NC, Cfg::TWM>(v, lay, t, tw, a.pre, pbar);
         if (!CONTIG && !Cfg::SINGLE && tid == 0) {
@@ -775,10 +800,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
             }
         }
 
-        if (a.post != 0) {
-            if (a.pre != 0) pbar.sync();
-            fft_dir<C, N, E, NC, Cfg::TWM>(v, lay, t, tw, a.post, pbar);
-        }
+        if (a.post != 0) fft_dir<C, N, E, NC, Cfg::TWM>(v, lay, t, tw, a.post, pbar);   // first writes wait inside
 
         if constexpr (CONTIG) {
             if constexpr (Cfg::SINGLE) {
@@ -800,7 +822,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
         } else {
             // Back into the landing layout, then one TMA store per box (clipped at
             // the lattice edge, so inactive pencils are never written).
-            if (a.pre != 0 || a.post != 0) __syncthreads();   // exchange reads are done
+            __syncthreads();   // landing and exchange reads are done
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 C *col = bufc + c * N * WP + w;

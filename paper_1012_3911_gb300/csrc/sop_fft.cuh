@@ -49,6 +49,26 @@ template <typename C> __device__ __forceinline__ C mk(decltype(C::x) re, decltyp
 }
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+// Complex64 sums and differences as one paired FP32 instruction (the
+// .f32x2 forms of sm_100 and later): both lanes round to nearest like two
+// scalar adds, so results are bit-identical, at half the issue slots of the
+// butterflies' additions.
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "add.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "sub.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
     return mk<C>(fmar(a.x, b.x, -(a.y * b.y)), fmar(a.x, b.y, a.y * b.x));
 }
@@ -547,17 +567,101 @@ __device__ __forceinline__ void fft_stage(C (&v)[E], const Lay &lay, int t, cons
     });
 }
 
+// The same stage split in two halves, for callers that synchronise between
+// them: the butterflies of every butterfly group of the thread (results back
+// into v in the natural order of the stage's outputs), then the writes of v
+// to the exchange row.
+template <typename C, int N, int E, int S>
+__device__ __forceinline__ void fft_stage_compute(C (&v)[E], int t, const StageTw<C, N, E, S> &tw) {
+    constexpr StagePlan P = make_plan(N, E);
+    constexpr int R = P.R[S];
+    constexpr int NS = P.NS[S];
+    constexpr int T = N / E;
+    constexpr int Q = E / R;
+    static_assert(E % R == 0, "radix must divide E");
+    sfor<0, Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        C x[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r] = v[q + r * Q];
+        if constexpr (NS > 1) {
+            sfor<1, R>([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                x[r] = tw_apply(x[r], tw.z[r - 1]);
+                if constexpr (NS > T) {
+                    constexpr int M = NS / T;
+                    constexpr int O = NS * R / T;
+                    x[r] = rotq<((q % M) * r) % O, O>(x[r]);
+                }
+            });
+        }
+        Dft<R>::run(x);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q + r * Q] = x[r];
+    });
+}
+template <typename C, int N, int E, int S, typename Lay>
+__device__ __forceinline__ void fft_stage_write(const C (&v)[E], const Lay &lay, int t) {
+    constexpr StagePlan P = make_plan(N, E);
+    constexpr int R = P.R[S];
+    constexpr int NS = P.NS[S];
+    constexpr int T = N / E;
+    constexpr int Q = E / R;
+    constexpr bool FASTW = LayFast<Lay>::value && write_split_ok<N, E, S, LayFast<Lay>::LR>();
+    if constexpr (FASTW) {
+        const unsigned ut = (unsigned)t;
+        const int b = NS <= T ? (int)((ut / NS) * NS * R + ut % NS) : t;
+        C *pw = lay.p + Lay::off(b);
+        sfor<0, Q>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            constexpr int j0 = T * q;
+            constexpr int ob0 = (j0 / NS) * NS * R + j0 % NS;
+            sfor<0, R>([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                pw[pad_off(ob0 + r * NS, LayFast<Lay>::LR)] = v[q + r * Q];
+            });
+        });
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int j = t + T * q;
+            const int ob = (j / NS) * NS * R + j % NS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) lay.st(ob + r * NS, v[q + r * Q]);
+        }
+    }
+}
+
 // Forward FFT of NC pencils held by this thread group, natural mapping in
 // and out.  Every thread of the CTA must call it (it contains barriers).
+//
+// SMEM & 8 ("late barrier"): the barrier that keeps a stage's writes from
+// overtaking other threads' reads of the previous exchange is taken after the
+// stage's butterflies, just before the writes, instead of right after the
+// reads, so a thread's arithmetic overlaps the other threads' reads.  Then
+// every stage's writes, including the first stage's, wait at that barrier,
+// and no barrier follows the last exchange: the caller must synchronise
+// before it overwrites the exchange rows by other means.
 // tw holds the twiddles of stage S; those of stage S+1 are fetched before the
 // exchange barrier.
 template <typename C, int N, int E, int NC, int S, int SMEM, typename Lay, typename Bar>
 __device__ __forceinline__ void fft_forward_from(C (&v)[NC][E], const Lay (&lay)[NC], int t, const C *__restrict__ tab,
                                                  const StageTw<C, N, E, S> &tw, const Bar &bar) {
     constexpr StagePlan P = make_plan(N, E);
+    constexpr bool LATEBAR = (SMEM & 8) != 0;
     if constexpr (S < P.S) {
+        if constexpr (LATEBAR) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) fft_stage<C, N, E, S>(v[c], lay[c], t, tw);
+            for (int c = 0; c < NC; ++c) fft_stage_compute<C, N, E, S>(v[c], t, tw);
+            if constexpr (S + 1 < P.S) {
+                bar.sync();   // every read of the previous exchange (or landing) is done
+#pragma unroll
+                for (int c = 0; c < NC; ++c) fft_stage_write<C, N, E, S>(v[c], lay[c], t);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) fft_stage<C, N, E, S>(v[c], lay[c], t, tw);
+        }
         if constexpr (S + 1 < P.S) {
             constexpr int T = N / E;
             StageTw<C, N, E, S + 1> nxt;
@@ -578,7 +682,7 @@ __device__ __forceinline__ void fft_forward_from(C (&v)[NC][E], const Lay (&lay)
 #pragma unroll
                     for (int m = 0; m < E; ++m) v[c][m] = lay[c].ld(t + T * m);
             }
-            bar.sync();
+            if constexpr (!LATEBAR) bar.sync();
             if constexpr ((SMEM & 4) != 0) nxt.template load<SMEM>(tab, t);
             fft_forward_from<C, N, E, NC, S + 1, SMEM>(v, lay, t, tab, nxt, bar);
         }

@@ -51,7 +51,7 @@ def fixture(cfg):
     # the stored values belong to these inputs (sums compared loosely: NumPy's
     # exp and sin may round differently on another platform)
     assert tuple(g["dims"]) == w.dims and int(g["n_steps"]) == w.n_steps and float(g["dt"]) == w.dt
-    assert abs(complex(g["psi0_sum"]) - complex(w.psi0.sum())) <= 1e-9 * abs(complex(g["psi0_sum"]))
+    assert abs(float(g["psi0_abs2"]) - float(np.sum(np.abs(w.psi0) ** 2))) <= 1e-9 * float(g["psi0_abs2"])
     assert abs(float(g["V_sum"]) - float(w.V.sum())) <= 1e-9 * abs(float(g["V_sum"]))
     assert abs(float(g["field_sum"]) - float(np.asarray(w.field).sum())) <= 1e-9 * max(1.0, abs(float(g["field_sum"])))
     return g
