@@ -145,7 +145,7 @@ def config_legs(args, sop, wl, torch, stream, flush, peak):
         if w.V is not None:
             q.set_potential(w.V)
         q.set_state(torch.from_numpy(w.psi0))
-        shapes = q.autotune(w.dt, 8) if tune else [0, 0]
+        shapes = q.autotune(w.dt, 32 if w.npoints < (1 << 24) else 4) if tune else [0, 0]
         F = None if w.field is None else np.asarray(w.field)[:n]
         q.step(min(4, n), w.dt, None if F is None else F[:min(4, n)])   # warm-up
         q.set_state(torch.from_numpy(w.psi0))
@@ -331,7 +331,7 @@ def main():
     psi0 = torch.from_numpy(w.psi0.astype(np.complex64)).cuda()
     prop.set_potential(w.V)
     prop.state.copy_(psi0)
-    pass_shapes = prop.autotune(w.dt, 16)   # launch shapes of the x and y passes (untimed)
+    pass_shapes = prop.autotune(w.dt, 64)   # launch shapes of the x and y passes (untimed)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def one_step(ev=None):
@@ -570,15 +570,19 @@ def main():
         torch.cuda.synchronize()
         t3d = e0.elapsed_time(e1) * 1e-3
         npt3 = n3 ** 3
-        # streamed bytes per step: 6 transform passes + 2 factor passes over 4 components
-        # (read + write, 8 B each), the per-momentum table (32 B) and FP32 V phase (8 B)
-        design3 = 8 * 2 * 4 * 8 * npt3 + 32 * npt3 + 8 * npt3
+        # streamed bytes per step of the fused design: 4 passes over the 4 components
+        # (read + write, 8 B each), the per-momentum table (32 B) and the V phase (8 B);
+        # B_min: two round trips of the spinor plus FP32 V
+        design3 = 4 * 2 * 4 * 8 * npt3 + 32 * npt3 + 8 * npt3
+        bmin3 = 2 * 2 * 4 * 8 * npt3 + 4 * npt3
         dirac3d = {"value": npt3 * T3 / t3d, "unit": UNIT, "dtype": "f32",
                    "workload": f"3D four-component Dirac, {n3}^3 on [-4,4)^3, soft core (a^2 0.01), "
                                f"A = (20 cos 2t, 5 sin 2t, 2), dt 1e-4, {T3} steps",
                    "us_per_step": t3d / T3 * 1e6,
                    "design_bytes_per_step": design3,
-                   "design_frac_of_peak": design3 / (t3d / T3) / 1e9 / measured_peaks()[0]}
+                   "design_frac_of_peak": design3 / (t3d / T3) / 1e9 / measured_peaks()[0],
+                   "b_min_bytes_per_step": bmin3,
+                   "b_min_frac": bmin3 / (t3d / T3) / 1e9 / measured_peaks()[0]}
         q3.close()
         torch.cuda.empty_cache()
         # 2D Dirac in a pulse travelling along x (A_y(x, t), the paper's

@@ -195,7 +195,7 @@ int64_t sop_launch_counter(sop_plan plan);
  * sop_autotune: times every shape of the contiguous-axis pass (x) and then of
  * the strided-axis passes (y, z) for this plan's lattice, component count
  * and dtype, over trial_steps split steps of size dt (<= 0: 16) with no
- * field, and keeps the fastest of each.  The trials run on a scratch copy of
+ * field (best of three trials), and keeps the fastest of each.  The trials run on a scratch copy of
  * the bound state (allocated like sop_energy's scratch if absent), so the
  * state is unchanged.  Results are cached per process for the lattice shape,
  * component count, dtype and device: a later plan of the same shape takes

@@ -29,6 +29,10 @@ UNITS = [
     ("pass_f32_strided", "sop_pass_inst.cu", ["-DSOP_REAL=float", "-DSOP_CONTIG=0"]),
     ("pass_f64_contig", "sop_pass_inst.cu", ["-DSOP_REAL=double", "-DSOP_CONTIG=1"]),
     ("pass_f64_strided", "sop_pass_inst.cu", ["-DSOP_REAL=double", "-DSOP_CONTIG=0"]),
+    ("pass4_f32_contig", "sop_pass4_inst.cu", ["-DSOP_REAL=float", "-DSOP_CONTIG=1"]),
+    ("pass4_f32_strided", "sop_pass4_inst.cu", ["-DSOP_REAL=float", "-DSOP_CONTIG=0"]),
+    ("pass4_f64_contig", "sop_pass4_inst.cu", ["-DSOP_REAL=double", "-DSOP_CONTIG=1"]),
+    ("pass4_f64_strided", "sop_pass4_inst.cu", ["-DSOP_REAL=double", "-DSOP_CONTIG=0"]),
     ("fso1d_f32", "sop_1d_inst.cu", ["-DSOP_REAL=float", "-DSOP_IS_DOUBLE=0"]),
     ("fso1d_f64", "sop_1d_inst.cu", ["-DSOP_REAL=double", "-DSOP_IS_DOUBLE=1"]),
 ] + [

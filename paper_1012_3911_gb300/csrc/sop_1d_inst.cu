@@ -86,6 +86,10 @@ template <typename Real, int N, int NC, bool CONTIG> int async_wp_fit() {
 }
 template <typename Real, int N> int async_wp_of(int nc, bool contig) {
     if (nc == 1) return contig ? async_wp_fit<Real, N, 1, true>() : async_wp_fit<Real, N, 1, false>();
+    if (nc == 4) {
+        if constexpr (N <= 1024) return contig ? async_wp_fit<Real, N, 4, true>() : async_wp_fit<Real, N, 4, false>();
+        return 0;
+    }
     return contig ? async_wp_fit<Real, N, 2, true>() : async_wp_fit<Real, N, 2, false>();
 }
 }  // namespace

@@ -387,7 +387,17 @@ int launch_pass(sop_plan p, const PassArgs &a0, int nc, const char *what) {
             cudaError_t e = cudaErrorInvalidValue;
             int64_t adv = 0;
             const int var = p->pass_var[contig ? 0 : 1][nc - 1];
-            if (var > 0 && var < kPassVariants) {
+            if (nc == 4) {
+                e = p->f64 ? (contig ? launch_async4_f64_contig(a, tm, p->stream, &adv)
+                                     : launch_async4_f64_strided(a, tm, p->stream, &adv))
+                           : (contig ? launch_async4_f32_contig(a, tm, p->stream, &adv)
+                                     : launch_async4_f32_strided(a, tm, p->stream, &adv));
+                if (e == cudaSuccess) {
+                    p->tile_base[0] += (unsigned long long)adv;
+                    return SOP_OK;
+                }
+                return cuda_fail(e, what);   // callers check fused_dirac3_ok first
+            } else if (var > 0 && var < kPassVariants) {
                 e = launch_async_variant(p->f64, contig, var, a, nc, tm, p->stream, &adv);
                 if (e == cudaErrorInvalidValue) cudaGetLastError();   // no such variant for the size
             }
@@ -805,6 +815,11 @@ int step_dirac3d(sop_plan p, int64_t n, double dt, const double *field, bool pro
                 M[i][j] = v;
             }
     };
+    // Fused form (four passes per step, 4x4 factors inside the x and z passes)
+    // where the four-component passes exist for the x and z sides; else the
+    // transforms run as batched passes with the factors as streaming passes.
+    const bool fused = p->async_passes && async_pencils_per_cta(p->f64, (int)p->dims[0], 4, true) > 0 &&
+                       async_pencils_per_cta(p->f64, (int)p->dims[2], 4, false) > 0;
     int64_t P0 = 0;
     for (int64_t P = 0; P <= n; ++P) {
         if (prof && (P - P0 == kProfileChunk || P == 0)) {
@@ -823,6 +838,43 @@ int step_dirac3d(sop_plan p, int64_t n, double dt, const double *field, bool pro
                 Md[2 * (4 * i + j) + 1] = v.imag();
             }
         const bool smp = step_sampled(p, P);
+        if (fused) {
+            // x pass with all four components: [inverse FFT_x] -> exp(-i V tau') M_P -> [FFT_x]
+            PassArgs a;
+            base_args(p, a, p->psi, 0);
+            a.pre = P > 0 ? +1 : 0;
+            a.post = P < n ? -1 : 0;
+            a.op = OP_D3V;
+            a.vtab = p->v_set ? ((P == 0 || P == n) ? p->vhalf : p->vfull) : nullptr;
+            if (prof) a.rows4 = profile_row(p, P, P0);
+            else std::memcpy(a.mix4, Md, sizeof(Md));
+            rc = run_pass(p, a, 4, 0, "3D Dirac real-space pass", smp);
+            if (rc) return rc;
+            if (P == n) break;
+            // y: forward transforms of the four components (a batch)
+            base_args(p, a, p->psi, 1);
+            a.n_batch = 4;
+            a.pre = -1;
+            a.op = OP_NONE;
+            rc = run_pass(p, a, 1, 2, "3D Dirac forward transform", smp);
+            if (rc) return rc;
+            // z pass with all four components: FFT_z -> U~ and 1/N -> inverse FFT_z
+            base_args(p, a, p->psi, 2);
+            a.pre = -1;
+            a.post = +1;
+            a.op = OP_D3T;
+            a.dtab = p->dtab;
+            rc = run_pass(p, a, 4, 1, "3D Dirac momentum-space pass", smp);
+            if (rc) return rc;
+            // y: inverse transforms
+            base_args(p, a, p->psi, 1);
+            a.n_batch = 4;
+            a.pre = +1;
+            a.op = OP_NONE;
+            rc = run_pass(p, a, 1, 2, "3D Dirac inverse transform", smp);
+            if (rc) return rc;
+            continue;
+        }
         {
             Bracket br(p, 0, smp);
             cudaError_t e = launch_dirac3_real(p->psi, p->npts, p->v_set ? ((P == 0 || P == n) ? p->vhalf : p->vfull)
@@ -1413,20 +1465,26 @@ int sop_autotune(sop_plan p, double dt, int trial_steps, int *chosen) {
     int best[2] = {0, 0};
     for (int kind = 0; kind < 2 && !rc; ++kind) {
         float best_ms = 0.f;
-        for (int v = 0; v < kPassVariants && !rc; ++v) {
+        const int nshapes = p->f64 ? 1 : kPassVariants;   // shapes 1.. exist for complex64 only
+        for (int v = 0; v < nshapes && !rc; ++v) {
             p->pass_var[kind][0] = p->pass_var[kind][1] = v;
             rc = step_impl(p, 2, dt, nullptr);   // warm-up (tables, tensor maps, attributes)
             if (rc) break;
-            cudaEventRecord(e0, p->stream);
-            rc = step_impl(p, trial_steps, dt, nullptr);
-            if (rc) break;
-            cudaEventRecord(e1, p->stream);
-            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
-                rc = cuda_fail(e, "cudaEventSynchronize");
-                break;
-            }
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
+            for (int rep = 0; rep < 3 && !rc; ++rep) {   // best of three trials
+                cudaEventRecord(e0, p->stream);
+                rc = step_impl(p, trial_steps, dt, nullptr);
+                if (rc) break;
+                cudaEventRecord(e1, p->stream);
+                if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+                    rc = cuda_fail(e, "cudaEventSynchronize");
+                    break;
+                }
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep == 0 || t < ms) ms = t;
+            }
+            if (rc) break;
             if (v == 0 || ms < best_ms) {
                 best_ms = ms;
                 best[kind] = v;

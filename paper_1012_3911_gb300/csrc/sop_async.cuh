@@ -94,13 +94,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     return true;
 }
 // The same with a caller-set limit (sop_set_wait_limit): polled with the
-// non-blocking probe, so even a limit of a few ns gives up on a copy still
-// in flight (try_wait may itself suspend for longer than such a limit).
+// non-blocking probe and timed on the SM's cycle counter (two cycles per ns,
+// the clock rounded down), so even a limit of a few ns gives up on a copy
+// still in flight; try_wait may suspend, and the global timer may advance in
+// steps, for longer than such a limit.
 __device__ __forceinline__ bool mbar_wait_limit(uint32_t bar, uint32_t parity, uint64_t limit_ns, bool custom) {
     if (!custom) return mbar_wait_bounded(bar, parity, limit_ns);
-    const uint64_t t0 = global_ns();
+    const long long c0 = clock64();
+    const long long lim = (long long)(limit_ns > (1ull << 40) ? (1ull << 41) : 2 * limit_ns);
     while (!mbar_test_wait(bar, parity))
-        if (global_ns() - t0 > limit_ns) return false;
+        if (clock64() - c0 > lim) return false;
     return true;
 }
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
@@ -229,7 +232,7 @@ template <typename Real, int N, int NC, bool CONTIG, int VAR = 0> struct AsyncCf
     static constexpr int CSZ = 2 * (int)sizeof(Real);
     static constexpr int PITCH = ((N + (N >> G::LR)) + 1) & ~1;   // even: rows stay 16-byte aligned
     static constexpr int wp_contig() {
-        int w = (Pol::CT > 0 ? Pol::CT : (Pol::WP1 ? 128 : 256)) / T;
+        int w = (Pol::CT > 0 ? Pol::CT : (Pol::WP1 || NC == 4 ? 128 : 256)) / T;
         return w < 1 ? 1 : w;
     }
     static constexpr int wp_strided() {
@@ -273,7 +276,9 @@ template <typename Real, int N, int NC, bool CONTIG, int VAR = 0> struct AsyncCf
     // (Measured on GB300: 2048^2 c128 split steps 1394 -> 1354 us; for
     // complex64 the second buffer is worth more than the extra CTA.)
     static constexpr int ctas_smem(size_t bytes) { return (int)((228 * 1024) / (bytes + 1024)); }
-    static constexpr bool SINGLE = Pol::NBUF == 1 ||
+    // Four-component passes also keep one buffer: their tiles are four times
+    // larger, and more CTAs per SM pay more than the prefetch.
+    static constexpr bool SINGLE = Pol::NBUF == 1 || (Pol::NBUF == 0 && NC == 4) ||
                                    (Pol::NBUF == 0 && SOP_SINGLE_BUFFER != 0 && !CONTIG && CSZ == 16 && NC == 1 &&
                                     ctas_smem(128 + BUF + TWZ + AXT) > ctas_smem(128 + 2 * BUF + TWZ + AXT));
     static constexpr int NBUF = SINGLE ? 1 : 2;
@@ -303,7 +308,7 @@ template <typename Real, int N, int NC, bool CONTIG, int VAR = 0> struct AsyncCf
     static constexpr int minb() {
         int b = (int)((227 * 1024) / (SMEM > 0 ? SMEM : 1));
         const int bt = 2048 / THREADS;
-        const int regs = VAR == 0 ? (LEAN ? 64 : 104) : Pol::REGS;
+        const int regs = VAR == 0 ? (NC == 4 ? 128 : (LEAN ? 64 : 104)) : Pol::REGS;
         const int br = 65536 / (THREADS * regs);   // registers per thread to leave
         if (bt < b) b = bt;
         if (br < b) b = br;
@@ -325,7 +330,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
     pass_kernel_async(const __grid_constant__ PassArgs a, const __grid_constant__ CUtensorMap tmap) {
     static_assert(!MULTI || NC == 1, "multi-instance passes have one component");
     using Cfg = AsyncCfg<Real, N, NC, CONTIG, VAR>;
-    constexpr bool VPRE = Cfg::Pol::VPRE;
+    constexpr bool VPRE = Cfg::Pol::VPRE && NC != 4;   // the 4x4 factor reads its phase values itself
     using C = cplx_t<Real>;
     using Ph = Phase<Real>;
     constexpr int E = Cfg::E, T = Cfg::T, WP = Cfg::WP, CSZ = Cfg::CSZ;
@@ -451,7 +456,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
     };
 
     auto comp_index = [&](int c, int64_t b) -> int64_t {
-        return NC == 1 ? b : (int64_t)a.pair_comp[pz][c];
+        return NC == 1 ? b : (NC == 2 ? (int64_t)a.pair_comp[pz][c] : (int64_t)c);
     };
 
     // Strided axes: the TMA boxes of tile tl of lattice q, f(component slot,
@@ -612,7 +617,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
         }
         const int64_t per_batch = pv_i64(dp, 0), total = pv_i64(dp, 1), n0 = pv_i64(dp, 2);
         const int64_t tiles_per_batch = pv_i64(dp, 7);
-        const bool want_v = CONTIG && pv_vtab(dp) != nullptr && (op_v || a.op == OP_DV);
+        const bool want_v = CONTIG && pv_vtab(dp) != nullptr && (op_v || a.op == OP_DV || a.op == OP_D3V);
         // Pencil of this thread: first point (linear index base) and lattice
         // coordinates co (0 along the pass axis).  Pencil and tile counts are
         // below 2^31, so the index arithmetic runs in 32 bits.
@@ -777,6 +782,8 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
                     }
                 }
             }
+        } else if constexpr (NC == 4) {
+            apply_op4<Real, E, T>(v, a, base, stride, t, want_v ? vt : nullptr);
         } else {
             if (a.op == OP_DV) {
                 // (psi_a, psi_b) <- exp(-i V tau') M (psi_a, psi_b) on this component pair

@@ -12,6 +12,7 @@
 //                    compact matrix per lattice column (k_mix_rows);
 //   momentum space:  psi~ <- (1/N) [cos(E tau) - i sin(E tau) H(p)/E] psi~,
 //                    H = c alpha.p + m c^2 beta (the closed form of Eq. 33).
+#include "sop_dirac4.cuh"
 #include "sop_kernels.cuh"
 #include "sop_internal.h"
 
@@ -76,36 +77,10 @@ __global__ void __launch_bounds__(kThreads) k_dirac3_real(cplx_t<Real> *psi, int
         C w[4];
         if (rows) {
             Real q[8];
-            const Real *r = rows + (j % nx) * 8;
-            if constexpr (sizeof(Real) == 4) {
-                const float4 x0 = __ldg(reinterpret_cast<const float4 *>(r)), x1 = __ldg(reinterpret_cast<const float4 *>(r) + 1);
-                q[0] = x0.x; q[1] = x0.y; q[2] = x0.z; q[3] = x0.w; q[4] = x1.x; q[5] = x1.y; q[6] = x1.z; q[7] = x1.w;
-            } else {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const double2 x = __ldg(reinterpret_cast<const double2 *>(r) + k);
-                    q[2 * k] = x.x;
-                    q[2 * k + 1] = x.y;
-                }
-            }
-            const Real a = q[0], b1 = q[1], b2 = q[2], b3 = q[3], d1 = q[4], d2 = q[5], d3 = q[6];
-            const C bm = mk<C>(b1, -b2), bp = mk<C>(b1, b2), dm = mk<C>(d1, -d2), dp = mk<C>(d1, d2);
-            // (b.alpha v) and (d.Sigma v), then w = a v + i (b.alpha v + d.Sigma v)
-            C u[4];
-            u[0] = cadd(cadd(cmul(bm, v[3]), cscale(v[2], b3)), cadd(cscale(v[0], d3), cmul(dm, v[1])));
-            u[1] = cadd(csub(cmul(bp, v[2]), cscale(v[3], b3)), csub(cmul(dp, v[0]), cscale(v[1], d3)));
-            u[2] = cadd(cadd(cmul(bm, v[1]), cscale(v[0], b3)), cadd(cscale(v[2], d3), cmul(dm, v[3])));
-            u[3] = cadd(csub(cmul(bp, v[0]), cscale(v[1], b3)), csub(cmul(dp, v[2]), cscale(v[3], d3)));
-#pragma unroll
-            for (int c = 0; c < 4; ++c) w[c] = cadd(cscale(v[c], a), mul_pi(u[c]));
+            dirac4_load_row(rows + (j % nx) * 8, q);
+            dirac4_mix_compact(q, v, w);
         } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                C acc = cmul(M.m[4 * i], v[0]);
-#pragma unroll
-                for (int k = 1; k < 4; ++k) acc = cadd(acc, cmul(M.m[4 * i + k], v[k]));
-                w[i] = acc;
-            }
+            dirac4_mix(M.m, v, w);
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) __stcg(psi + c * npts + j, vtab ? Ph::apply(w[c], f) : w[c]);
@@ -164,28 +139,12 @@ __global__ void __launch_bounds__(kThreads) k_dirac3_kinetic(cplx_t<Real> *psi, 
     using C = cplx_t<Real>;
     for (int64_t k = (int64_t)blockIdx.x * kThreads + threadIdx.x; k < npts; k += (int64_t)gridDim.x * kThreads) {
         Real co, sm, sx, sy, sz;
-        if constexpr (sizeof(Real) == 4) {
-            const float4 a = __ldcg(reinterpret_cast<const float4 *>(tab) + 2 * k);
-            const float4 b = __ldcg(reinterpret_cast<const float4 *>(tab) + 2 * k + 1);
-            co = a.x; sm = a.y; sx = a.z; sy = a.w; sz = b.x;
-        } else {
-            const double2 a = __ldcg(reinterpret_cast<const double2 *>(tab) + 4 * k);
-            const double2 b = __ldcg(reinterpret_cast<const double2 *>(tab) + 4 * k + 1);
-            const double2 d = __ldcg(reinterpret_cast<const double2 *>(tab) + 4 * k + 2);
-            co = a.x; sm = a.y; sx = b.x; sy = b.y; sz = d.x;
-        }
+        dirac4_load_kin(tab, k, co, sm, sx, sy, sz);
         C v[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) v[c] = __ldcg(psi + c * npts + k);
-        const C dm = mk<C>(co, -sm), dp = mk<C>(co, sm);      // cos -+ i sin mu
-        const C uz = mk<C>(Real(0), -sz), vz = mk<C>(Real(0), sz);   // -i sin kz, +i sin kz
-        const C um = mk<C>(-sy, -sx);                          // -i sin km
-        const C up = mk<C>(sy, -sx);                           // -i sin kp
         C r[4];
-        r[0] = cadd(cmul(dm, v[0]), cadd(cmul(uz, v[2]), cmul(um, v[3])));
-        r[1] = cadd(cmul(dm, v[1]), cadd(cmul(up, v[2]), cmul(vz, v[3])));
-        r[2] = cadd(cmul(uz, v[0]), cadd(cmul(um, v[1]), cmul(dp, v[2])));
-        r[3] = cadd(cmul(up, v[0]), cadd(cmul(vz, v[1]), cmul(dp, v[3])));
+        dirac4_kinetic(co, sm, sx, sy, sz, v, r);
 #pragma unroll
         for (int c = 0; c < 4; ++c) __stcg(psi + c * npts + k, scale2(r[c], shi, slo));
     }

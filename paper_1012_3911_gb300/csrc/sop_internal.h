@@ -14,6 +14,8 @@ enum PassOp : int {
     OP_T = 2,     // Schroedinger momentum-space factor (Eq. 13) and 1/N
     OP_DV = 3,    // Dirac real-space factor (Eqs. 21-26), one component pair
     OP_DT = 4,    // Dirac momentum-space factor (Eq. 33 in closed form) and 1/N
+    OP_D3V = 5,   // 3D Dirac real-space factor on all four components (Eqs. 21-26, 4x4)
+    OP_D3T = 6,   // 3D Dirac momentum-space factor on all four components and 1/N
 };
 
 // Arguments of one pencil pass along one axis.  A "pencil" is the set of
@@ -46,6 +48,10 @@ struct PassArgs {
     // OP_DV: 2x2 complex block per component pair (re, im of m00, m01, m10, m11)
     double mix[2][8];
     int pair_comp[2][2];     // component indices of each pair
+    // OP_D3V: the merged 4x4 mixing (row-major re, im) or, with rows4 set, the
+    // compact mixing row (8 reals, plan precision) of each x_1 column
+    double mix4[32];
+    const void *rows4;
     // Persistent asynchronous passes (filled by the launcher)
     int *errflag;            // device word; bit 1 set when a bounded wait gave up
     uint64_t wait_ns;        // limit of the tile-copy waits (0: kWaitLimitNs)
@@ -149,6 +155,16 @@ cudaError_t launch_async_f64_contig(const PassArgs &a, int nc, const TensorMapBy
                                  int64_t *ctr_advance);
 cudaError_t launch_async_f64_strided(const PassArgs &a, int nc, const TensorMapBytes &tmap, cudaStream_t s,
                                  int64_t *ctr_advance);
+// Four-component passes of the 3D Dirac step (sop_pass4_inst.cu, sides up to
+// 1024); cudaErrorInvalidValue for a side without a kernel that fits an SM.
+cudaError_t launch_async4_f32_contig(const PassArgs &a, const TensorMapBytes &tmap, cudaStream_t s,
+                                     int64_t *ctr_advance);
+cudaError_t launch_async4_f32_strided(const PassArgs &a, const TensorMapBytes &tmap, cudaStream_t s,
+                                      int64_t *ctr_advance);
+cudaError_t launch_async4_f64_contig(const PassArgs &a, const TensorMapBytes &tmap, cudaStream_t s,
+                                     int64_t *ctr_advance);
+cudaError_t launch_async4_f64_strided(const PassArgs &a, const TensorMapBytes &tmap, cudaStream_t s,
+                                      int64_t *ctr_advance);
 // Launch-shape variants 1 .. kPassVariants - 1 of the persistent pass
 // (sop_pass_var.cu, complex64 only); cudaErrorInvalidValue for a size, dtype
 // or variant without a kernel.

@@ -13,6 +13,7 @@
 
 #include <type_traits>
 
+#include "sop_dirac4.cuh"
 #include "sop_fft.cuh"
 #include "sop_internal.h"
 
@@ -192,6 +193,61 @@ __device__ __forceinline__ void apply_op(cplx_t<Real> (&v)[NC][E], const PassArg
                 v[0][m] = scale2(r0, shi, slo);
                 v[1][m] = scale2(r1, shi, slo);
             }
+        }
+    }
+}
+
+// The four-component factors of the 3D Dirac step on the E values per
+// component a thread holds (axis index i = t + T m of the pencil at linear
+// point index base; stride along the axis).  OP_D3V runs on the contiguous
+// x pass: vrow are the pencil's phase values (global, or null) and a.rows4
+// the per-column mixing rows indexed by x = i.  OP_D3T reads the
+// per-momentum table a.dtab at base + i stride.
+template <typename Real, int E, int T>
+__device__ __forceinline__ void apply_op4(cplx_t<Real> (&v)[4][E], const PassArgs &a, int64_t base, int64_t stride,
+                                          int t, const cplx_t<Real> *vrow) {
+    using C = cplx_t<Real>;
+    using Ph = Phase<Real>;
+    if (a.op == OP_D3V) {
+        const Real *rows = reinterpret_cast<const Real *>(a.rows4);
+        C M[16];
+        if (!rows) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) M[q] = mk<C>(Real(a.mix4[2 * q]), Real(a.mix4[2 * q + 1]));
+        }
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int i = t + T * m;
+            const C x[4] = {v[0][m], v[1][m], v[2][m], v[3][m]};
+            C w[4];
+            if (rows) {
+                Real q[8];
+                dirac4_load_row(rows + (int64_t)i * 8, q);
+                dirac4_mix_compact(q, x, w);
+            } else {
+                dirac4_mix(M, x, w);
+            }
+            if (vrow) {
+                const C f = ld_stream(vrow + i);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) w[c] = Ph::apply(w[c], f);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c][m] = w[c];
+        }
+    } else if (a.op == OP_D3T) {
+        const Real *tab = reinterpret_cast<const Real *>(a.dtab);
+        const Real shi = Real(a.scale_hi), slo = Real(a.scale_lo);
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int64_t k = base + (int64_t)(t + T * m) * stride;
+            Real co, sm, sx, sy, sz;
+            dirac4_load_kin(tab, k, co, sm, sx, sy, sz);
+            const C x[4] = {v[0][m], v[1][m], v[2][m], v[3][m]};
+            C r[4];
+            dirac4_kinetic(co, sm, sx, sy, sz, x, r);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c][m] = scale2(r[c], shi, slo);
         }
     }
 }

@@ -19,12 +19,17 @@ def _gpu(orc):
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
-@pytest.mark.parametrize("dims", [(512, 384), (64, 48, 96)])
+@pytest.mark.parametrize("dims", [(2048, 2048), (128, 192, 256)])
 def test_bounded_wait_gives_up_then_the_plan_recovers(dtype, dims):
+    """Lattices with several tiles per CTA and single-buffer launch shapes
+    (complex128 strided passes keep one buffer by default), so that each CTA
+    waits for a tile whose copy was issued just before the wait."""
     w = gc.random_workload(dims, 1, seed=31 + len(dims), n_steps=4, dt=0.01, field_scale=0.05)
     prop = sop.Propagator(w.dims, w.spacing, 1, dtype)
     prop.set_state(torch.from_numpy(w.psi0))
     prop.set_potential(w.V)
+    prop.set_pass_shape(0, 1)   # one pencil group per CTA, one tile buffer
+    prop.set_pass_shape(1, 1)
     sop.sop_set_wait_limit(prop.plan, 1)
     status = None
     for _ in range(5):   # a wait gives up unless every copy landed before its first poll
