@@ -432,6 +432,18 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         tb = e0.elapsed_time(e1) * 1e-3
+        # the same batch with every step launched directly (no replayed graph)
+        os.environ["SOP_BATCH_GRAPH"] = "0"
+        bat_d = sop.Batch(props)
+        os.environ.pop("SOP_BATCH_GRAPH")
+        bat_d.step(2, ws[0].dt, [f[:2] for f in fields])
+        flush.fill_(1.0)
+        e0.record(stream)
+        bat_d.step(args.batch_steps, ws[0].dt, fields)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        td = e0.elapsed_time(e1) * 1e-3
+        bat_d.close()
         flush.fill_(1.0)
         e0.record(stream)
         for q, x in zip(props, ws):
@@ -442,7 +454,10 @@ def main():
         batched = {"value": npts5 * args.batch_steps / tb, "unit": UNIT, "dtype": "f32",
                    "workload": f"64 independent 2D Schroedinger lattices, sides from 256..2048 (radix 2 and 3), "
                                f"{npts5} points in all, {args.batch_steps} lockstep split steps (sop_batch_step)",
-                   "one_plan_at_a_time": npts5 * args.batch_steps / ts}
+                   "one_plan_at_a_time": npts5 * args.batch_steps / ts,
+                   "direct_launches": npts5 * args.batch_steps / td,
+                   "time_loop": "middle steps replayed as one captured CUDA graph per step (size groups on "
+                                "concurrent streams); first and last step launched directly"}
         # adjoint gradient of |<phi|psi_N>|^2 on one instance of that workload
         x = ws[0]
         q = props[0]

@@ -1528,6 +1528,20 @@ struct sop_batch_s {
     unsigned long long tile_base = 0;
     InstDesc *desc = nullptr;
     size_t desc_cap = 0;   // descriptors
+    // One merged middle step as a CUDA graph: the size groups of each pass kind
+    // run concurrently on side streams, each on its own tile counter (reset at
+    // the start of every replay); the field row is a device word the graph
+    // advances.  Captured once per descriptor buffer and replayed per step.
+    cudaGraphExec_t step_exec = nullptr;
+    const InstDesc *exec_desc = nullptr;
+    int exec_kernels = 0;
+    std::vector<cudaStream_t> side;
+    cudaStream_t cap = nullptr;   // capture stream
+    std::vector<cudaEvent_t> evs;
+    unsigned long long *gctr = nullptr;
+    size_t gctr_cap = 0;
+    int64_t *row_dev = nullptr;
+    bool graphs = true;   // SOP_BATCH_GRAPH=0 turns the replayed graph off (direct launches)
 };
 
 namespace {
@@ -1535,16 +1549,39 @@ namespace {
 int batch_free(sop_batch b) {
     if (!b) return SOP_OK;
     cudaStreamSynchronize(b->stream);
+    if (b->step_exec) cudaGraphExecDestroy(b->step_exec);
+    for (cudaStream_t st : b->side) cudaStreamDestroy(st);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (cudaEvent_t ev : b->evs) cudaEventDestroy(ev);
     dfree(b->tile_ctr);
     dfree(b->desc);
+    dfree(b->gctr);
+    dfree(b->row_dev);
     delete b;
     return SOP_OK;
+}
+
+// One multi-instance pass of a replayed step on stream st with its own counter.
+cudaError_t batch_launch_on(sop_batch b, PassArgs &a, bool contig, cudaStream_t st, unsigned long long *ctr) {
+    sop_plan p0 = b->plans[0];
+    a.errflag = p0->errflag;
+    a.wait_ns = p0->wait_ns;
+    a.tile_ctr = ctr;
+    a.tile_base[0] = a.tile_base[1] = 0;
+    a.n_comp_total = 1;
+    TensorMapBytes tm;
+    std::memset(&tm, 0, sizeof(tm));
+    int64_t adv = 0;
+    if (b->f64)
+        return contig ? launch_async_f64_contig(a, 1, tm, st, &adv) : launch_async_f64_strided(a, 1, tm, st, &adv);
+    return contig ? launch_async_f32_contig(a, 1, tm, st, &adv) : launch_async_f32_strided(a, 1, tm, st, &adv);
 }
 
 // One multi-instance pass over the lattices of a group.
 int batch_launch(sop_batch b, PassArgs &a, bool contig, const char *what) {
     sop_plan p0 = b->plans[0];
     a.errflag = p0->errflag;
+    a.wait_ns = p0->wait_ns;
     a.tile_ctr = b->tile_ctr;
     a.tile_base[0] = a.tile_base[1] = b->tile_base;
     a.n_comp_total = 1;
@@ -1586,6 +1623,10 @@ int sop_batch_create(sop_batch *out, int n_plans, const sop_plan *plans) {
     b->plans.assign(plans, plans + n_plans);
     b->stream = plans[0]->stream;
     b->f64 = plans[0]->f64;
+    {
+        const char *env = std::getenv("SOP_BATCH_GRAPH");
+        b->graphs = !(env && std::string(env) == "0");
+    }
     int rc = dalloc(&b->tile_ctr, 2 * sizeof(unsigned long long), "batch tile counters");
     if (!rc) {
         cudaError_t e = cudaMemsetAsync(b->tile_ctr, 0, 2 * sizeof(unsigned long long), b->stream);
@@ -1717,6 +1758,149 @@ int sop_batch_step(sop_batch b, int64_t n, double dt, const double *const *field
         }
         return launch_pass(p, a, 1, what);
     };
+    // One real-space index P launched directly on the batch stream: the x
+    // passes of every size group, then (P < n) the y passes.
+    auto direct_step = [&](int64_t P, int64_t P0) -> int {
+        int rc2 = SOP_OK;
+        for (auto &kv : gx) {
+            Group &g = kv.second;
+            if (!g.multi) {
+                for (int i : g.members)
+                    if ((rc2 = single(i, 0, P > 0 ? +1 : 0, P < n ? -1 : 0, OP_V, P, P0, "real-space pass"))) return rc2;
+                continue;
+            }
+            sop_plan p0 = b->plans[g.members[0]];
+            PassArgs a;
+            base_args(p0, a, p0->psi, 0);
+            a.pre = P > 0 ? +1 : 0;
+            a.post = P < n ? -1 : 0;
+            a.op = OP_V;
+            a.inst = b->desc + g.first;
+            a.n_inst = (int)g.members.size();
+            a.P = P;
+            a.p_table0 = P0;
+            a.n_total = n;
+            a.n_tiles = g.tiles;
+            if ((rc2 = batch_launch(b, a, true, "batched real-space pass"))) return rc2;
+        }
+        if (P == n) return SOP_OK;
+        for (auto &kv : gy) {
+            Group &g = kv.second;
+            if (!g.multi) {
+                for (int i : g.members)
+                    if ((rc2 = single(i, 1, -1, +1, OP_T, P, P0, "momentum-space pass"))) return rc2;
+                continue;
+            }
+            sop_plan p0 = b->plans[g.members[0]];
+            PassArgs a;
+            base_args(p0, a, p0->psi, 1);
+            a.pre = -1;
+            a.post = +1;
+            a.op = OP_T;
+            a.inst = b->desc + g.first;
+            a.n_inst = (int)g.members.size();
+            a.P = P;
+            a.p_table0 = P0;
+            a.n_total = n;
+            a.n_tiles = g.tiles;
+            if ((rc2 = batch_launch(b, a, false, "batched momentum-space pass"))) return rc2;
+        }
+        return SOP_OK;
+    };
+
+    // The merged middle step (0 < P < n) as a replayed graph: every group is a
+    // multi-instance launch, so its arguments do not depend on P; the field
+    // row comes from b->row_dev.
+    bool all_multi = !hd.empty();
+    for (auto *gm : {&gx, &gy})
+        for (auto &kv : *gm) all_multi = all_multi && kv.second.multi;
+    const size_t ngroups = gx.size() + gy.size();
+    auto ensure_graph = [&]() -> int {
+        if (b->step_exec && b->exec_desc == b->desc) return SOP_OK;
+        if (b->step_exec) {
+            cudaGraphExecDestroy(b->step_exec);
+            b->step_exec = nullptr;
+        }
+        int rc2 = SOP_OK;
+        if (b->gctr_cap < ngroups) {
+            dfree(b->gctr);
+            b->gctr = nullptr;
+            b->gctr_cap = 0;
+            if ((rc2 = dalloc(&b->gctr, ngroups * 2 * sizeof(unsigned long long), "batch group counters"))) return rc2;
+            b->gctr_cap = ngroups;
+        }
+        if (!b->row_dev && (rc2 = dalloc(&b->row_dev, sizeof(int64_t), "batch step row"))) return rc2;
+        const size_t nside = std::max(gx.size(), gy.size());
+        while (b->side.size() < nside) {
+            cudaStream_t st;
+            cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
+            b->side.push_back(st);
+        }
+        while (b->evs.size() < 2 * nside + 2) {
+            cudaEvent_t ev;
+            cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreateWithFlags");
+            b->evs.push_back(ev);
+        }
+        // captured on a stream of its own (the batch stream may be the legacy
+        // default stream, which cannot be captured); launched on the batch stream
+        if (!b->cap) {
+            cudaError_t e0 = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+            if (e0 != cudaSuccess) return cuda_fail(e0, "cudaStreamCreateWithFlags");
+        }
+        cudaStream_t cs = b->cap;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        int kernels = 0;
+        auto phase = [&](std::map<int64_t, Group> &gm, bool contig, size_t ctr0, cudaEvent_t fork) -> cudaError_t {
+            cudaError_t e2 = cudaEventRecord(fork, cs);
+            size_t k = 0;
+            for (auto &kv : gm) {
+                Group &g = kv.second;
+                cudaStream_t st = b->side[k];
+                if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(st, fork, 0);
+                sop_plan p0 = b->plans[g.members[0]];
+                PassArgs a;
+                base_args(p0, a, p0->psi, contig ? 0 : 1);
+                a.pre = contig ? +1 : -1;
+                a.post = contig ? -1 : +1;
+                a.op = contig ? OP_V : OP_T;
+                a.inst = b->desc + g.first;
+                a.n_inst = (int)g.members.size();
+                a.P = 1;
+                a.p_table0 = 0;
+                a.n_total = n;
+                a.n_tiles = g.tiles;
+                a.row_dev = b->row_dev;
+                if (e2 == cudaSuccess) e2 = batch_launch_on(b, a, contig, st, b->gctr + 2 * (ctr0 + k));
+                ++kernels;
+                cudaEvent_t join = b->evs[2 + 2 * k + (contig ? 0 : 1)];
+                if (e2 == cudaSuccess) e2 = cudaEventRecord(join, st);
+                if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(cs, join, 0);
+                ++k;
+            }
+            return e2;
+        };
+        e = cudaMemsetAsync(b->gctr, 0, ngroups * 2 * sizeof(unsigned long long), cs);
+        if (e == cudaSuccess) e = phase(gx, true, 0, b->evs[0]);
+        if (e == cudaSuccess) e = phase(gy, false, gx.size(), b->evs[1]);
+        if (e == cudaSuccess) e = advance_counter(b->row_dev, cs);
+        cudaGraph_t graph = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = ee;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->step_exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->step_exec = nullptr;
+            return cuda_fail(e, "capturing the batched step graph");
+        }
+        b->exec_desc = b->desc;
+        b->exec_kernels = kernels + 1;
+        return SOP_OK;
+    };
+    const bool use_graph = b->graphs && all_multi;
+
     for (int64_t P0 = 0; P0 <= n; P0 += kFieldChunk) {
         const int64_t P1 = std::min<int64_t>(n + 1, P0 + kFieldChunk);
         for (int i = 0; i < np; ++i) {
@@ -1728,51 +1912,22 @@ int sop_batch_step(sop_batch b, int64_t n, double dt, const double *const *field
             if (e != cudaSuccess) return cuda_fail(e, "build_field_tables");
             p->launches += 1;
         }
-        for (int64_t P = P0; P < P1; ++P) {
-            for (auto &kv : gx) {
-                Group &g = kv.second;
-                if (!g.multi) {
-                    for (int i : g.members)
-                        if ((rc = single(i, 0, P > 0 ? +1 : 0, P < n ? -1 : 0, OP_V, P, P0, "real-space pass"))) return rc;
-                    continue;
-                }
-                sop_plan p0 = b->plans[g.members[0]];
-                PassArgs a;
-                base_args(p0, a, p0->psi, 0);
-                a.pre = P > 0 ? +1 : 0;
-                a.post = P < n ? -1 : 0;
-                a.op = OP_V;
-                a.inst = b->desc + g.first;
-                a.n_inst = (int)g.members.size();
-                a.P = P;
-                a.p_table0 = P0;
-                a.n_total = n;
-                a.n_tiles = g.tiles;
-                if ((rc = batch_launch(b, a, true, "batched real-space pass"))) return rc;
-            }
-            if (P == n) break;
-            for (auto &kv : gy) {
-                Group &g = kv.second;
-                if (!g.multi) {
-                    for (int i : g.members)
-                        if ((rc = single(i, 1, -1, +1, OP_T, P, P0, "momentum-space pass"))) return rc;
-                    continue;
-                }
-                sop_plan p0 = b->plans[g.members[0]];
-                PassArgs a;
-                base_args(p0, a, p0->psi, 1);
-                a.pre = -1;
-                a.post = +1;
-                a.op = OP_T;
-                a.inst = b->desc + g.first;
-                a.n_inst = (int)g.members.size();
-                a.P = P;
-                a.p_table0 = P0;
-                a.n_total = n;
-                a.n_tiles = g.tiles;
-                if ((rc = batch_launch(b, a, false, "batched momentum-space pass"))) return rc;
-            }
+        int64_t P = P0;
+        if (P == 0) {
+            if ((rc = direct_step(0, P0))) return rc;
+            P = 1;
         }
+        const int64_t mid_end = std::min<int64_t>(P1, n);   // middle indices P < n of this chunk
+        if (use_graph && mid_end - P >= 2) {
+            if ((rc = ensure_graph())) return rc;
+            const int64_t Pstart = P;
+            cudaError_t e = set_counter(b->row_dev, P - P0, b->stream);
+            for (; e == cudaSuccess && P < mid_end; ++P) e = cudaGraphLaunch(b->step_exec, b->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch(batched step)");
+            b->plans[0]->launches += (int64_t)b->exec_kernels * (mid_end - Pstart) + 1;
+        }
+        for (; P < P1; ++P)
+            if ((rc = direct_step(P, P0))) return rc;
     }
     return SOP_OK;
 }

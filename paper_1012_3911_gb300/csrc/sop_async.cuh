@@ -399,15 +399,20 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
         if constexpr (MULTI) return reinterpret_cast<C *>(d->psi);
         else return reinterpret_cast<C *>(a.psi);
     };
+    // Field row of this launch's real-space index and whether it takes the
+    // half factor (first and last index of a call); a graph-replayed middle
+    // step reads its row from a device word (set after griddep_wait).
+    int64_t frow = a.P - a.p_table0;
+    const bool half_v = a.row_dev == nullptr && (a.P == 0 || a.P == a.n_total);
     auto pv_vtab = [&](const InstDesc *d) -> const C * {
-        if constexpr (MULTI) return reinterpret_cast<const C *>((a.P == 0 || a.P == a.n_total) ? d->vhalf : d->vfull);
+        if constexpr (MULTI) return reinterpret_cast<const C *>(half_v ? d->vhalf : d->vfull);
         else return reinterpret_cast<const C *>(a.vtab);
     };
     auto pv_row = [&](const InstDesc *d, int ax) -> const C * {   // factor row of axis ax (field or kinetic)
         if constexpr (MULTI) {
             if (!op_v) return reinterpret_cast<const C *>(d->ttab[ax]);
             if (!d->ftab || d->foff[ax] < 0) return nullptr;
-            return reinterpret_cast<const C *>(d->ftab) + (a.P - a.p_table0) * d->frow_len + d->foff[ax];
+            return reinterpret_cast<const C *>(d->ftab) + frow * d->frow_len + d->foff[ax];
         } else {
             return reinterpret_cast<const C *>(op_v ? a.ftab[ax] : a.ttab[ax]);
         }
@@ -550,6 +555,8 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
     // unfinished and the tile counters are behind): do nothing until the
     // host, which reports SOP_ETIMEOUT, has reset them.
     if (*reinterpret_cast<volatile int *>(a.errflag) != 0) return;
+    if constexpr (MULTI)
+        if (a.row_dev) frow = *reinterpret_cast<const volatile int64_t *>(a.row_dev);
     // Thread 0 claims one tile ahead: the claim for the tile after the
     // current one is made when the current one is issued, so the latency of
     // the atomic is hidden behind a whole tile.  Claims stop after the first

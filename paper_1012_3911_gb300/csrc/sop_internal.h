@@ -68,6 +68,10 @@ struct PassArgs {
     const InstDesc *inst;
     int n_inst;
     int64_t P, p_table0, n_total;
+    // Graph-replayed steps: when set, the launch is a merged middle step
+    // (full real-space factor) whose field row P - p_table0 is read from this
+    // device word (advanced by the replayed graph itself) instead of P.
+    const int64_t *row_dev;
     int64_t n_tiles;         // tiles of the pass (per component pair for nc == 2)
     int64_t n_xgroups;       // strided: tiles along x
     int64_t o_stride;        // strided: element stride of the remaining coordinate
@@ -209,6 +213,10 @@ cudaError_t launch_grad_v(const double *acc, bool f64, int64_t npts, double zr, 
 // out == nullptr returns its entry count, else fills out from tw (async);
 // -1 for a size without persistent passes.
 int stage_table_f32(int n, int nc, void *out, const void *tw, cudaStream_t s);
+// *p = v, and *p += 1, each one single-thread kernel on s (the step row of
+// graph-replayed batched steps).
+cudaError_t set_counter(int64_t *p, int64_t v, cudaStream_t s);
+cudaError_t advance_counter(int64_t *p, cudaStream_t s);
 int stage_table_f64(int n, int nc, void *out, const void *tw, cudaStream_t s);
 // Pencils per CTA of the asynchronous pass (the tensor-map box width for
 // strided axes); 0 when that pass does not fit on an SM (one-shot passes).

@@ -210,4 +210,19 @@ cudaError_t convert_potential(double *out, const void *in, int64_t n, bool in_f6
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void k_set_counter(int64_t *p, int64_t v) { *p = v; }
+__global__ void k_advance_counter(int64_t *p) { *p += 1; }
+}  // namespace
+
+cudaError_t set_counter(int64_t *p, int64_t v, cudaStream_t s) {
+    k_set_counter<<<1, 1, 0, s>>>(p, v);
+    return cudaGetLastError();
+}
+
+cudaError_t advance_counter(int64_t *p, cudaStream_t s) {
+    k_advance_counter<<<1, 1, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
 }  // namespace sop

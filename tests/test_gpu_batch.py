@@ -93,3 +93,27 @@ def test_batch_rejections():
             sop.sop_batch_create(plans)
     for p in (p64, p128, dirac, three):
         p.close()
+
+
+@pytest.mark.parametrize("n", [7, 530])
+def test_replayed_step_graph_equals_direct_launches(n, monkeypatch):
+    """The merged middle steps replayed as a captured graph (size groups on
+    concurrent streams, the field row from a device word) give bit-identical
+    states to direct launches, within one field chunk and across a chunk
+    boundary (530 > 512 rows)."""
+    import torch
+    sides = [(256, 384), (384, 256), (512, 512), (256, 256)]
+    ws = [wl.config5_instance(k, sides=s, n_steps=n) for k, s in enumerate(sides)]
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("SOP_BATCH_GRAPH", mode)
+        props = _props(ws, "c64")
+        b = sop.Batch(props)
+        b.step(n, ws[0].dt, [w.field for w in ws])
+        torch.cuda.synchronize()
+        out[mode] = [p.state.clone() for p in props]
+        b.close()
+        for p in props:
+            p.close()
+    for g, d in zip(out["1"], out["0"]):
+        assert torch.equal(g, d)
