@@ -59,6 +59,7 @@ def parse_args():
     ap.add_argument("--batch-steps", type=int, default=400, help="split steps of the batched / adjoint / spectral sample")
     ap.add_argument("--configs", type=int, default=1,
                     help="also time configs 1, 3, 4 and config 2 in FP64 at full size and length (0: skip)")
+    ap.add_argument("--pass-shapes", default=None, help="'C,S': fixed launch shapes instead of sop_autotune")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
@@ -84,7 +85,8 @@ def kernel_source_hash() -> str:
 
 # The sources the pencil-pass kernels are compiled from (device code and the
 # argument structures); host-side driver files do not change them.
-PASS_KERNEL_FILES = ("sop_async.cuh", "sop_fft.cuh", "sop_kernels.cuh", "sop_internal.h", "sop_pass_inst.cu")
+PASS_KERNEL_FILES = ("sop_async.cuh", "sop_fft.cuh", "sop_kernels.cuh", "sop_internal.h", "sop_pass_inst.cu",
+                     "sop_pass_var.cu", "sop_dirac4.cuh")
 
 
 def pass_kernel_hash() -> str:
@@ -331,7 +333,12 @@ def main():
     psi0 = torch.from_numpy(w.psi0.astype(np.complex64)).cuda()
     prop.set_potential(w.V)
     prop.state.copy_(psi0)
-    pass_shapes = prop.autotune(w.dt, 64)   # launch shapes of the x and y passes (untimed)
+    if args.pass_shapes:   # fixed shapes (profiling runs), else the autotuner's choice
+        pass_shapes = [int(v) for v in args.pass_shapes.split(",")]
+        prop.set_pass_shape(0, pass_shapes[0])
+        prop.set_pass_shape(1, pass_shapes[1])
+    else:
+        pass_shapes = prop.autotune(w.dt, 64)   # launch shapes of the x and y passes (untimed)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def one_step(ev=None):
@@ -742,7 +749,8 @@ def main():
                                    f"sin^2 laser along x, {S} split steps of dt=0.02 per benchmark step",
                        "lattice": [args.n, args.n], "split_steps_per_step": S,
                        "ms_per_split_step": total_ms / args.steps / S,
-                       "pass_shapes": {"x": pass_shapes[0], "y": pass_shapes[1], "chosen_by": "sop_autotune"},
+                       "pass_shapes": {"x": pass_shapes[0], "y": pass_shapes[1],
+                                       "chosen_by": "--pass-shapes" if args.pass_shapes else "sop_autotune"},
                        "l2": "flushed (256 MiB write) before every timed step; psi + V tables stay L2-resident "
                              "within a step",
                        "parallelism": f"replicas x{world} (independent problems, no data-path collective)"},

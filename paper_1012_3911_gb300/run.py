@@ -33,6 +33,8 @@ def main(argv=None):
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--steps", default="3,2", help="comma-separated chunks of split steps")
     ap.add_argument("--no-energy", action="store_true")
+    ap.add_argument("--shape", default=None,
+                    help="launch shapes 'C,S' of the contiguous and strided passes (default: shape 0)")
     ap.add_argument("--spectral", type=int, default=0,
                     help="run the spectral method with eigenfunctions at this many energies (<= 16)")
     ap.add_argument("--dirac3d", action="store_true", help="3D four-component Dirac packet")
@@ -97,6 +99,10 @@ def main(argv=None):
     kw = {} if args.n is None else {"n": args.n}
     w = wl.CONFIGS[args.config](n_steps=max(1, sum(chunks)), **kw)
     p = Propagator(w.dims, w.spacing, w.comps, args.dtype)
+    if args.shape:
+        sc, ss = (int(v) for v in args.shape.split(","))
+        p.set_pass_shape(0, sc)
+        p.set_pass_shape(1, ss)
     p.set_state(torch.from_numpy(w.psi0))
     if w.V is not None:
         p.set_potential(w.V)
