@@ -181,8 +181,11 @@ __host__ __device__ constexpr int largest_divisor_le(int n, int cap) {
 //   AXL1  : only the pass-axis factor row is read through L1
 //   CT    : threads per CTA on the contiguous axis (0: 128 with WP1, else 256)
 template <int VAR> struct PassPolicy;
+//   PMAJOR: strided axes with pencil-major threads (each pencil's threads are
+//           whole warps, so its exchanges synchronise only its own warps;
+//           the lane-interleaved landing reads then touch two bank lines)
 struct PolBase {
-    static constexpr bool LATE = false, AXL1 = false;
+    static constexpr bool LATE = false, AXL1 = false, PMAJOR = false;
     static constexpr int E = 0, CT = 0;
 };
 template <> struct PassPolicy<0> : PolBase {
@@ -194,8 +197,8 @@ template <> struct PassPolicy<1> : PolBase {
     static constexpr int NBUF = 1, REGS = 80;
 };
 template <> struct PassPolicy<2> : PolBase {
-    static constexpr bool WP1 = true, VPRE = false, L1TAB = true;
-    static constexpr int NBUF = 1, REGS = 64;
+    static constexpr bool WP1 = true, VPRE = false, L1TAB = true, PMAJOR = true;
+    static constexpr int NBUF = 2, REGS = 80;
 };
 template <> struct PassPolicy<3> : PolBase {
     static constexpr bool WP1 = true, VPRE = false, L1TAB = true;
@@ -302,7 +305,8 @@ template <typename Real, int N, int NC, bool CONTIG, int VAR = 0> struct AsyncCf
     static constexpr int TWM = (LEAN ? 2 : 1) | (Pol::LATE ? 4 : 0) | 8;
     // On the contiguous axis a pencil is whole warps (threadIdx.y = pencil), so
     // its exchanges synchronise only its own warps (named barrier 1 + pencil).
-    static constexpr bool PENCIL_BAR = CONTIG && T % 32 == 0 && WP > 1 && WP <= 15;
+    static constexpr bool PMAJOR = !CONTIG && Pol::PMAJOR && T % 32 == 0 && WP > 1 && WP <= 15;
+    static constexpr bool PENCIL_BAR = (CONTIG || PMAJOR) && T % 32 == 0 && WP > 1 && WP <= 15;
     static_assert(USED <= PITCH && USED <= RPITCH, "exchange rows must not overlap");
     // CTAs per SM that shared memory allows; the register budget follows.
     static constexpr int minb() {
@@ -342,8 +346,8 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
     C *axt = reinterpret_cast<C *>(smem + Cfg::OFF_AXT);   // pass-axis factor table
 
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int t = CONTIG ? (int)threadIdx.x : tid / WP;   // thread within the pencil
-    const int w = CONTIG ? (int)threadIdx.y : tid % WP;   // pencil within the tile
+    const int t = (CONTIG || Cfg::PMAJOR) ? (int)threadIdx.x : tid / WP;   // thread within the pencil
+    const int w = (CONTIG || Cfg::PMAJOR) ? (int)threadIdx.y : tid % WP;   // pencil within the tile
     const int pz = NC == 2 ? (int)blockIdx.z : 0;
     const int64_t stride = CONTIG ? 1 : a.stride;
     const bool op_v = a.op == OP_V, op_t = a.op == OP_T;
@@ -708,7 +712,10 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
             }
         }
         // the landing rows become exchange rows: a transform's first writes
-        // wait at its late barrier until every landing read is done
+        // wait at its late barrier until every landing read is done (with
+        // pencil-major threads the landing rows hold every pencil's values,
+        // so all of the CTA's reads must be done first)
+        if constexpr (Cfg::PMAJOR) __syncthreads();
 
         if (a.pre != 0) fft_dir<C, N, E, NC, Cfg::TWM>(v, lay, t, tw, a.pre, pbar);
         if (!CONTIG && !Cfg::SINGLE && tid == 0) {
