@@ -178,6 +178,124 @@ __global__ void __launch_bounds__(kThreads) k_accum(const C *a, const C *b, int6
     }
 }
 
+// One checkpoint segment at once: slots k < count of lam and psi hold the
+// costate and the state at step m0 + k.  For every k the block sums
+// <lam_k|psi_k> and <lam_k|X_a|psi_k> (products in the state's precision,
+// float pairs over the warp, FP64 per warp slot and block, fixed order) into
+// partial[(k gridDim.x + block) 8 + v]; every point adds
+// sum_k w_k conj(lam_k) psi_k to its accumulator once (w = 1 for step 0,
+// else 2), instead of once per step.
+constexpr int kSegPts = 4;   // points per thread and chunk
+
+template <typename C>
+__global__ void __launch_bounds__(kThreads) k_seg_reduce(const C *__restrict__ lam, const C *__restrict__ psi,
+                                                         int64_t npts, int count, int64_t m0, InnerGeom g,
+                                                         double2 *acc, double *partial) {
+    using R = decltype(C{}.x);
+    constexpr bool kPair = sizeof(R) == 4;
+    using A = typename std::conditional<kPair, float4, double2>::type;
+    extern __shared__ double wsum[];   // [warp][count][kVals]
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < (kThreads / 32) * count * kVals; i += kThreads) wsum[i] = 0.0;
+    __syncthreads();
+    R x0[3], hh[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        x0[ax] = (R)g.x0[ax];
+        hh[ax] = (R)g.h[ax];
+    }
+    const int64_t span = (int64_t)kThreads * kSegPts;
+    for (int64_t base = (int64_t)blockIdx.x * span; base < npts; base += (int64_t)gridDim.x * span) {
+        R xs[kSegPts][3];
+        PairSum<R> ax_[kSegPts], ay_[kSegPts];   // sum_k w_k conj(lam) psi per point
+#pragma unroll
+        for (int q = 0; q < kSegPts; ++q) {
+            uint32_t r = (uint32_t)(base + threadIdx.x + (int64_t)q * kThreads);
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                xs[q][ax] = R(0);
+                if (ax < g.ndim) {
+                    const uint32_t n = (uint32_t)g.dims[ax];
+                    const uint32_t i = r % n;
+                    r /= n;
+                    xs[q][ax] = x0[ax] + (R)i * hh[ax];
+                }
+            }
+        }
+        for (int k = 0; k < count; ++k) {
+            const R w = (m0 + k == 0) ? R(1) : R(2);
+            R loc[kVals];
+#pragma unroll
+            for (int v = 0; v < kVals; ++v) loc[v] = R(0);
+#pragma unroll
+            for (int q = 0; q < kSegPts; ++q) {
+                const int64_t j = base + threadIdx.x + (int64_t)q * kThreads;
+                if (j < npts) {
+                    const C u = lam[(int64_t)k * npts + j], vv = psi[(int64_t)k * npts + j];
+                    const R re = u.x * vv.x + u.y * vv.y;   // conj(u) v
+                    const R im = u.x * vv.y - u.y * vv.x;
+                    ax_[q].add(w * re);
+                    ay_[q].add(w * im);
+                    loc[0] += re;
+                    loc[1] += im;
+#pragma unroll
+                    for (int ax = 0; ax < 3; ++ax) {
+                        loc[2 + 2 * ax] += xs[q][ax] * re;
+                        loc[3 + 2 * ax] += xs[q][ax] * im;
+                    }
+                }
+            }
+            PairSum<R> ps[kVals];
+#pragma unroll
+            for (int v = 0; v < kVals; ++v) ps[v].add(loc[v]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int v = 0; v < kVals; ++v) ps[v].add(ps[v].shfl_xor(o));
+            if (lane == 0)
+#pragma unroll
+                for (int v = 0; v < kVals; ++v) wsum[(wid * count + k) * kVals + v] += ps[v].value();
+        }
+        A *ac = reinterpret_cast<A *>(acc);
+#pragma unroll
+        for (int q = 0; q < kSegPts; ++q) {
+            const int64_t j = base + threadIdx.x + (int64_t)q * kThreads;
+            if (j < npts) {
+                A sacc = ac[j];
+                if constexpr (kPair) {
+                    float hx, ex, hy, ey;
+                    two_sum(sacc.x, ax_[q].hi, hx, ex);
+                    two_sum(sacc.y, ay_[q].hi, hy, ey);
+                    sacc = make_float4(hx, hy, sacc.z + (ex + ax_[q].lo), sacc.w + (ey + ay_[q].lo));
+                } else {
+                    sacc.x += ax_[q].hi;
+                    sacc.y += ay_[q].hi;
+                }
+                ac[j] = sacc;
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < count * kVals; i += kThreads) {
+        double sum = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) sum += wsum[w * count * kVals + i];
+        const int k = i / kVals, v = i % kVals;
+        partial[((int64_t)k * gridDim.x + blockIdx.x) * kVals + v] = sum;
+    }
+}
+
+// out[(m0 + k) 8 + v] = scale * sum over the nb blocks of slot k (block k,
+// warp v, fixed order).
+__global__ void k_seg_final(const double *partial, int nb, double scale, double *out, int64_t m0) {
+    const int k = blockIdx.x, v = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (v < kVals) {
+        double sum = 0.0;
+        for (int i = lane; i < nb; i += 32) sum += partial[((int64_t)k * nb + i) * kVals + v];
+        sum = warp_sum(sum);
+        if (lane == 0) out[(m0 + k) * kVals + v] = scale * sum;
+    }
+}
+
 // Spectral method.  Per time sample, k_spectral_sample forms the partial
 // sums of conj(psi0_j) psi_j (products in the state's precision, summed over
 // kUnroll points per thread in that precision, then as a float pair per
@@ -411,6 +529,39 @@ cudaError_t launch_inner(const void *a, const void *b, bool f64, int ndim, const
         k_inner<float2><<<kBlocks, kThreads, 0, s>>>(static_cast<const float2 *>(a), static_cast<const float2 *>(b),
                                                        npts, g, partial);
     k_inner_final<<<1, 32 * kVals, 0, s>>>(partial, kBlocks, dV, out);
+    return cudaGetLastError();
+}
+
+constexpr int kSegMax = 64;   // slots per k_seg_reduce launch (shared memory: 512 B per slot)
+
+int seg_partials(int count) { return (count < kSegMax ? count : kSegMax) * kBlocks * kVals; }
+
+cudaError_t launch_seg_reduce(const void *lam, const void *psi, bool f64, int count, int64_t m0, int ndim,
+                              const int64_t *dims, const double *h, double dV, double *acc, double *partial,
+                              double *out, cudaStream_t s) {
+    InnerGeom g{};
+    g.ndim = ndim;
+    int64_t npts = 1;
+    for (int ax = 0; ax < 3; ++ax) {
+        g.dims[ax] = ax < ndim ? dims[ax] : 1;
+        g.h[ax] = ax < ndim ? h[ax] : 0.0;
+        g.x0[ax] = ax < ndim ? -0.5 * (double)dims[ax] * h[ax] : 0.0;
+        npts *= g.dims[ax];
+    }
+    double2 *ac = reinterpret_cast<double2 *>(acc);
+    for (int k0 = 0; k0 < count; k0 += kSegMax) {
+        const int c = count - k0 < kSegMax ? count - k0 : kSegMax;
+        const size_t smem = (size_t)(kThreads / 32) * c * kVals * sizeof(double);
+        if (f64)
+            k_seg_reduce<double2><<<kBlocks, kThreads, smem, s>>>(static_cast<const double2 *>(lam) + k0 * npts,
+                                                                  static_cast<const double2 *>(psi) + k0 * npts,
+                                                                  npts, c, m0 + k0, g, ac, partial);
+        else
+            k_seg_reduce<float2><<<kBlocks, kThreads, smem, s>>>(static_cast<const float2 *>(lam) + k0 * npts,
+                                                                 static_cast<const float2 *>(psi) + k0 * npts,
+                                                                 npts, c, m0 + k0, g, ac, partial);
+        k_seg_final<<<c, 32 * kVals, 0, s>>>(partial, kBlocks, dV, out, m0 + k0);
+    }
     return cudaGetLastError();
 }
 

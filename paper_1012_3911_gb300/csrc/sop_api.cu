@@ -1967,13 +1967,14 @@ int sop_adjoint_gradient(sop_plan p, const void *phi_dev, int64_t n_steps, doubl
     const size_t sb = (size_t)p->npts * p->csz;
     const int64_t K = (N + every - 1) / every;           // checkpoints at 0, every, 2 every, ...
     const int64_t S = std::min<int64_t>(every, N) + 1;   // states of one recomputed segment
-    char *ck = nullptr, *seg = nullptr, *lam = nullptr;
+    char *ck = nullptr, *seg = nullptr, *lam = nullptr, *lseg = nullptr;
     double *sdev = nullptr, *cdev = nullptr, *acc = nullptr, *part = nullptr;
     auto cleanup = [&]() {
         cudaStreamSynchronize(p->stream);
         dfree(ck);
         dfree(seg);
         dfree(lam);
+        dfree(lseg);
         dfree(sdev);
         dfree(cdev);
         dfree(acc);
@@ -1982,10 +1983,12 @@ int sop_adjoint_gradient(sop_plan p, const void *phi_dev, int64_t n_steps, doubl
     rc = dalloc(&ck, (size_t)K * sb, "adjoint checkpoints");
     if (!rc) rc = dalloc(&seg, (size_t)S * sb, "adjoint segment");
     if (!rc) rc = dalloc(&lam, sb, "adjoint costate");
+    if (!rc) rc = dalloc(&lseg, (size_t)S * sb, "adjoint costate segment");
     if (!rc) rc = dalloc(&sdev, (size_t)(N + 1) * 8 * sizeof(double), "adjoint overlaps");
     if (!rc) rc = dalloc(&cdev, 8 * sizeof(double), "adjoint target overlap");
     if (!rc) rc = dalloc(&acc, (size_t)p->npts * 2 * sizeof(double), "adjoint accumulator");
-    if (!rc) rc = dalloc(&part, (size_t)inner_partials() * sizeof(double), "adjoint partials");
+    if (!rc) rc = dalloc(&part, (size_t)std::max(inner_partials(), seg_partials((int)std::min<int64_t>(every, N))) *
+                                    sizeof(double), "adjoint partials");
     if (rc) {
         cleanup();
         return rc;
@@ -2040,13 +2043,21 @@ int sop_adjoint_gradient(sop_plan p, const void *phi_dev, int64_t n_steps, doubl
                 if ((r = copy(slot(seg, k + 1), slot(seg, k)))) return r;
                 if ((r = step_on(p, slot(seg, k + 1), dt, n0 + k))) return r;
             }
-            for (int64_t m = n1; m > n0; --m) {
-                // lambda_{m-1} = U_{m-1}^dagger lambda_m: the step with -dt
-                if ((r = step_on(p->rev, lam, -dt, m - 1))) return r;
-                const void *psi_m1 = slot(seg, m - 1 - n0);
-                if ((r = inner(lam, psi_m1, sdev + (m - 1) * 8))) return r;
-                if ((r = accum(lam, psi_m1, m - 1 == 0 ? 1.0 : 2.0))) return r;
+            // costates lambda_{m-1} = U_{m-1}^dagger lambda_m (the step with -dt)
+            // into slots m - 1 - n0, then the whole segment's overlaps and
+            // accumulation in one reduction
+            const int64_t L = n1 - n0;
+            if ((r = copy(slot(lseg, L - 1), lam))) return r;
+            if ((r = step_on(p->rev, slot(lseg, L - 1), -dt, n1 - 1))) return r;
+            for (int64_t k = L - 2; k >= 0; --k) {
+                if ((r = copy(slot(lseg, k), slot(lseg, k + 1)))) return r;
+                if ((r = step_on(p->rev, slot(lseg, k), -dt, n0 + k))) return r;
             }
+            cudaError_t e = launch_seg_reduce(lseg, seg, p->f64, (int)L, n0, nd, p->dims, p->h, dV, acc, part, sdev,
+                                              p->stream);
+            p->launches += 2;
+            if (e != cudaSuccess) return cuda_fail(e, "adjoint segment reduction");
+            if ((r = copy(lam, slot(lseg, 0)))) return r;
         }
         return SOP_OK;
     };

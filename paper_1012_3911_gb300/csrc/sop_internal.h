@@ -181,6 +181,15 @@ cudaError_t launch_async_variant(bool f64, bool contig, int var, const PassArgs 
 int inner_partials();
 cudaError_t launch_inner(const void *a, const void *b, bool f64, int ndim, const int64_t *dims, const double *h,
                          double dV, double *partial, double *out, cudaStream_t s);
+// A whole checkpoint segment: for k < count, slots k of lam and psi (count
+// consecutive lattices each) hold the costate and the state of step m0 + k;
+// writes the 8 values of launch_inner for each step into out + (m0 + k) 8 and
+// adds sum_k w_k conj(lam_k) psi_k to acc (w = 1 for step 0, else 2).
+// partial holds seg_partials(count) doubles.
+int seg_partials(int count);
+cudaError_t launch_seg_reduce(const void *lam, const void *psi, bool f64, int count, int64_t m0, int ndim,
+                              const int64_t *dims, const double *h, double dV, double *acc, double *partial,
+                              double *out, cudaStream_t s);
 // acc_j += w conj(a_j) b_j, 16 bytes per point: complex128 (f64) or, for
 // complex64 states, the float pair (hi.re, hi.im, lo.re, lo.im) that
 // launch_grad_v reads back
