@@ -129,6 +129,10 @@ struct sop_plan_s {
 
     int gauge = SOP_GAUGE_LENGTH;   // meaning of the Schroedinger field samples
     void *ftab = nullptr;           // kFieldChunk rows x row_len
+    void *ftab_h = nullptr;         // half-step field rows (materialising calls): 2 x kFieldChunk x row_len
+    size_t ftab_h_cap = 0;
+    double *fvh = nullptr;          // their field vectors, 2 x (n+1) x ndim
+    int64_t fvh_cap = 0;
     int64_t row_len = 0;
     int64_t foff[3] = {0, 0, 0};
     double *fvec = nullptr;         // device field vectors, (n+1) x ndim
@@ -277,6 +281,8 @@ int plan_free(sop_plan p) {
     dfree(p->mtab);
     dfree(p->theta);
     dfree(p->ftab);
+    dfree(p->ftab_h);
+    dfree(p->fvh);
     dfree(p->fvec);
     dfree(p->partial);
     dfree(p->result);
@@ -958,12 +964,47 @@ int step_dirac2d(sop_plan p, int64_t n, double dt, const double *field) {
 }
 
 // Schroedinger, 1D/2D/3D, length or velocity gauge.
-int step_schrodinger(sop_plan p, int64_t n, double dt, const double *field) {
+// mat_base != null (length gauge, ndim >= 2): the state after each step P of
+// 1 .. n-1 is also written to mat_base + P mat_stride bytes (the real-space
+// pass of index P applies the two half factors separately and stores the
+// state between them).
+int step_schrodinger(sop_plan p, int64_t n, double dt, const double *field, void *mat_base = nullptr,
+                     int64_t mat_stride = 0) {
     const int nd = p->ndim;
     int rc = SOP_OK;
     FieldRows fr;
     rc = prepare_fields(p, n, dt, field, fr);
     if (rc) return rc;
+    const bool mat = mat_base != nullptr && nd >= 2 && p->gauge == SOP_GAUGE_LENGTH;
+    if (mat && fr.any) {
+        // field vectors of the two halves met at P: k f_{P-1} and k f_P
+        const double kf = -p->prm.charge * dt / (2.0 * p->prm.hbar);
+        const int64_t need = 2 * (n + 1) * nd;
+        if (p->fvh_cap < need) {
+            cudaStreamSynchronize(p->stream);
+            dfree(p->fvh);
+            p->fvh = nullptr;
+            p->fvh_cap = 0;
+            if ((rc = dalloc(&p->fvh, (size_t)need * sizeof(double), "half-step field vectors"))) return rc;
+            p->fvh_cap = need;
+        }
+        std::vector<double> fv((size_t)need);
+        for (int64_t P = 0; P <= n; ++P)
+            for (int a = 0; a < nd; ++a) {
+                fv[P * nd + a] = kf * field_sample(field, n, nd, P - 1, a);
+                fv[(n + 1) * nd + P * nd + a] = kf * field_sample(field, n, nd, P, a);
+            }
+        if ((rc = upload(p, p->fvh, fv.data(), need))) return rc;
+        const size_t bytes = (size_t)2 * kFieldChunk * fr.row_len * p->csz;
+        if (p->ftab_h_cap < bytes) {
+            cudaStreamSynchronize(p->stream);
+            dfree(p->ftab_h);
+            p->ftab_h = nullptr;
+            p->ftab_h_cap = 0;
+            if ((rc = dalloc(&p->ftab_h, bytes, "half-step field tables"))) return rc;
+            p->ftab_h_cap = bytes;
+        }
+    }
     const int *active = fr.active;
     const bool any_field = fr.any;
     const int64_t *offs = fr.offs;
@@ -984,11 +1025,25 @@ int step_schrodinger(sop_plan p, int64_t n, double dt, const double *field) {
                                 : build_field_tables(p->ftab, p->fvec + P0 * nd, P1 - P0, nd, p->dims, p->h, active,
                                                      offs, row_len, p->f64, p->stream);
             if (e != cudaSuccess) return cuda_fail(e, "field tables");
+            if (mat) {
+                char *h = static_cast<char *>(p->ftab_h);
+                e = build_field_tables(h, p->fvh + P0 * nd, P1 - P0, nd, p->dims, p->h, active, offs, row_len, p->f64,
+                                       p->stream);
+                if (e == cudaSuccess)
+                    e = build_field_tables(h + (size_t)kFieldChunk * row_len * p->csz, p->fvh + (n + 1 + P0) * nd,
+                                           P1 - P0, nd, p->dims, p->h, active, offs, row_len, p->f64, p->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "half-step field tables");
+            }
             br.done();
         }
         auto frow = [&](int64_t P, int a) -> const void * {
             if (!rfield || !active[a]) return nullptr;
             return static_cast<const char *>(p->ftab) + ((P - P0) * row_len + offs[a]) * p->csz;
+        };
+        auto hrow = [&](int half, int64_t P, int a) -> const void * {   // half 0: k f_{P-1}, 1: k f_P
+            if (!rfield || !active[a]) return nullptr;
+            return static_cast<const char *>(p->ftab_h) +
+                   (((size_t)half * kFieldChunk + (P - P0)) * row_len + offs[a]) * p->csz;
         };
         auto krow = [&](int64_t P, int a) -> const void * {
             if (!kfield || !active[a]) return p->kin[a];
@@ -1025,6 +1080,14 @@ int step_schrodinger(sop_plan p, int64_t n, double dt, const double *field) {
             a.op = OP_V;
             a.vtab = p->v_set ? ((P == 0 || P == n) ? p->vhalf : p->vfull) : nullptr;
             for (int ax = 0; ax < nd; ++ax) a.ftab[ax] = frow(P, ax);
+            if (mat && P > 0 && P < n) {
+                a.mat_out = static_cast<char *>(mat_base) + P * mat_stride;
+                a.vtab = p->v_set ? p->vhalf : nullptr;
+                for (int ax = 0; ax < nd; ++ax) {
+                    a.ftab[ax] = hrow(0, P, ax);
+                    a.fh2[ax] = hrow(1, P, ax);
+                }
+            }
             const bool smp = step_sampled(p, P);
             rc = run_pass(p, a, 1, 0, "real-space pass", smp);
             if (rc) return rc;
@@ -1080,6 +1143,15 @@ int step_impl(sop_plan p, int64_t n, double dt, const double *field) {
     if (p->comps == 4 && p->ndim == 3) return step_dirac3d(p, n, dt, field, prof);
     if (p->comps == 4) return prof ? step_dirac2d_profile(p, n, dt) : step_dirac2d(p, n, dt, field);
     return step_schrodinger(p, n, dt, field);
+}
+
+// A Schroedinger step sequence (length gauge, ndim >= 2) that also writes the
+// state after each step P = 1 .. n-1 to mat_base + P mat_stride bytes.
+int step_impl_mat(sop_plan p, int64_t n, double dt, const double *field, void *mat_base, int64_t mat_stride) {
+    if (n <= 0) return SOP_OK;
+    int rc = ensure_tables(p, dt);
+    if (rc) return rc;
+    return step_schrodinger(p, n, dt, field, mat_base, mat_stride);
 }
 
 int read_result(sop_plan p, int count, double *out) {
@@ -2036,23 +2108,44 @@ int sop_adjoint_gradient(sop_plan p, const void *phi_dev, int64_t n_steps, doubl
         if ((r = copy(lam, phi_dev))) return r;
         if ((r = accum(lam, work, 1.0))) return r;
         // backward sweep, one checkpoint segment at a time
+        std::vector<double> frev((size_t)std::min<int64_t>(every, N) * nd);
         for (int64_t s = K - 1; s >= 0; --s) {
             const int64_t n0 = s * every, n1 = std::min<int64_t>(N, n0 + every);
-            if ((r = copy(slot(seg, 0), slot(ck, s)))) return r;
-            for (int64_t k = 0; k + 1 < n1 - n0; ++k) {   // states n0 .. n1 - 1 (psi_{n1} is not needed again)
-                if ((r = copy(slot(seg, k + 1), slot(seg, k)))) return r;
-                if ((r = step_on(p, slot(seg, k + 1), dt, n0 + k))) return r;
-            }
-            // costates lambda_{m-1} = U_{m-1}^dagger lambda_m (the step with -dt)
-            // into slots m - 1 - n0, then the whole segment's overlaps and
-            // accumulation in one reduction
             const int64_t L = n1 - n0;
-            if ((r = copy(slot(lseg, L - 1), lam))) return r;
-            if ((r = step_on(p->rev, slot(lseg, L - 1), -dt, n1 - 1))) return r;
-            for (int64_t k = L - 2; k >= 0; --k) {
-                if ((r = copy(slot(lseg, k), slot(lseg, k + 1)))) return r;
-                if ((r = step_on(p->rev, slot(lseg, k), -dt, n0 + k))) return r;
+            if ((r = copy(slot(seg, 0), slot(ck, s)))) return r;
+            if (nd >= 2) {
+                // states n0 .. n1 - 1 from one merged call of L - 1 steps on slot
+                // L - 1 that writes the states in between into slots 1 .. L - 2
+                if (L > 1) {
+                    if ((r = copy(slot(seg, L - 1), slot(ck, s)))) return r;
+                    p->psi = slot(seg, L - 1);
+                    if ((r = step_impl_mat(p, L - 1, dt, F ? F + n0 * nd : nullptr, seg, (int64_t)sb))) return r;
+                }
+                // costates lambda_{n1-1} .. lambda_{n0} from one merged call of L
+                // steps with -dt and the field rows reversed (U_m^dagger is the
+                // step with -dt); the state after P steps, lambda_{n1-P}, lands
+                // in slot L - P
+                if ((r = copy(slot(lseg, 0), lam))) return r;
+                if (F)
+                    for (int64_t k = 0; k < L; ++k)
+                        for (int a = 0; a < nd; ++a) frev[(size_t)(k * nd + a)] = F[(n1 - 1 - k) * nd + a];
+                p->rev->psi = slot(lseg, 0);
+                if ((r = step_impl_mat(p->rev, L, -dt, F ? frev.data() : nullptr, slot(lseg, L), -(int64_t)sb)))
+                    return r;
+            } else {
+                for (int64_t k = 0; k + 1 < L; ++k) {   // states n0 .. n1 - 1 (psi_{n1} is not needed again)
+                    if ((r = copy(slot(seg, k + 1), slot(seg, k)))) return r;
+                    if ((r = step_on(p, slot(seg, k + 1), dt, n0 + k))) return r;
+                }
+                // costates lambda_{m-1} = U_{m-1}^dagger lambda_m (the step with -dt)
+                if ((r = copy(slot(lseg, L - 1), lam))) return r;
+                if ((r = step_on(p->rev, slot(lseg, L - 1), -dt, n1 - 1))) return r;
+                for (int64_t k = L - 2; k >= 0; --k) {
+                    if ((r = copy(slot(lseg, k), slot(lseg, k + 1)))) return r;
+                    if ((r = step_on(p->rev, slot(lseg, k), -dt, n0 + k))) return r;
+                }
             }
+            // the whole segment's overlaps and potential-gradient accumulation in one reduction
             cudaError_t e = launch_seg_reduce(lseg, seg, p->f64, (int)L, n0, nd, p->dims, p->h, dV, acc, part, sdev,
                                               p->stream);
             p->launches += 2;

@@ -723,8 +723,37 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
             claim_next();
         }
 
+        if constexpr (NC == 1 && CONTIG && !MULTI) {
+            if (op_v && a.mat_out) {
+                // psi_P = A_{P-1} u, stored; then A_P psi_P (A = half factor,
+                // phase values and field rows of each half)
+                const C *h1[3], *h2[3];
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) {
+                    h1[ax] = ax < a.ndim ? reinterpret_cast<const C *>(a.ftab[ax]) : nullptr;
+                    h2[ax] = ax < a.ndim ? reinterpret_cast<const C *>(a.fh2[ax]) : nullptr;
+                }
+                C g1 = Ph::one(), g2 = Ph::one();
+#pragma unroll
+                for (int ax = 1; ax < 3; ++ax) {
+                    if (h1[ax]) g1 = Ph::combine(g1, ldg_c(h1[ax] + co[ax]));
+                    if (h2[ax]) g2 = Ph::combine(g2, ldg_c(h2[ax] + co[ax]));
+                }
+                C *const mo = reinterpret_cast<C *>(a.mat_out) + coff[0] + base + t;
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const C vh = vph(m);
+                    C f1 = Ph::combine(vh, g1), f2 = Ph::combine(vh, g2);
+                    if (h1[0]) f1 = Ph::combine(ldg_c(h1[0] + t + T * m), f1);
+                    if (h2[0]) f2 = Ph::combine(ldg_c(h2[0] + t + T * m), f2);
+                    const C ps = Ph::apply(v[0][m], f1);
+                    if (active) st_stream(mo + T * m, ps);
+                    v[0][m] = Ph::apply(ps, f2);
+                }
+            }
+        }
         if constexpr (NC == 1) {
-            if (op_v || op_t) {
+            if ((op_v || op_t) && !(CONTIG && !MULTI && op_v && a.mat_out)) {
                 // Pencil-constant part g from the other axes' tables (absent when
                 // none is set), per-point part from the axis table and, for the
                 // real-space factor, the phase values.  The flags are uniform, so

@@ -40,6 +40,12 @@ struct PassArgs {
     const void *vtab;
     // OP_V: per-axis field phase tables of this pass (null = axis has no field)
     const void *ftab[3];
+    // OP_V with mat_out set (contiguous single-lattice passes): the state
+    // between the two half factors is written to mat_out.  vtab is then the
+    // half-step phase table, ftab the field rows of the trailing half of the
+    // previous step and fh2 those of the leading half of this one.
+    void *mat_out;
+    const void *fh2[3];
     // OP_T: per-axis kinetic tables
     const void *ttab[3];
     // OP_DT: per-momentum table (cos, sin*mc^2/E, sin*c p_x/E, sin*c p_y/E)
