@@ -51,7 +51,7 @@ def test_dirac1d_matches_oracle(orc, dtype, n, steps):
     ref = orc.dirac1d_propagate(psi0, V, sp, dt, steps, A)
     out, p = _gpu_run(n, sp, psi0, V, dt, steps, A, dtype)
     p.close()
-    tol = gc.TOL_F64 if dtype == "c128" else (gc.TOL_F32_FULL if steps >= 100 else gc.TOL_F32_SHORT * 5)
+    tol = gc.TOL_F64 if dtype == "c128" else (gc.TOL_F32_FULL if steps >= 100 else gc.TOL_F32_SHORT)
     assert out.shape == (2, n)
     assert gc.relerr(out, ref) < tol, gc.relerr(out, ref)
 
@@ -63,7 +63,7 @@ def test_dirac1d_no_field_no_potential(orc, dtype):
     ref = orc.dirac1d_propagate(psi0, None, sp, 1e-4, steps)
     out, p = _gpu_run(n, sp, psi0, None, 1e-4, steps, None, dtype)
     p.close()
-    assert gc.relerr(out, ref) < (gc.TOL_F64 if dtype == "c128" else gc.TOL_F32_SHORT * 5)
+    assert gc.relerr(out, ref) < (gc.TOL_F64 if dtype == "c128" else gc.TOL_F32_SHORT)
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])

@@ -68,7 +68,7 @@ def test_dirac3d_128_vs_oracle(orc, dtype):
     p.step(2, 1e-4, A)
     out = p.state.cpu().numpy().astype(np.complex128)
     p.close()
-    assert gc.relerr(out, ref) < (gc.TOL_F64 if dtype == "c128" else gc.TOL_F32_SHORT * 5)
+    assert gc.relerr(out, ref) < (gc.TOL_F64 if dtype == "c128" else gc.TOL_F32_SHORT)
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
@@ -90,4 +90,4 @@ def test_dirac_pulse_1024_vs_oracle(orc, dtype):
     p.step(2, w.dt, A)
     out = p.state.cpu().numpy().astype(np.complex128)
     p.close()
-    assert gc.relerr(out, ref) < (gc.TOL_F64 if dtype == "c128" else gc.TOL_F32_SHORT * 5)
+    assert gc.relerr(out, ref) < (gc.TOL_F64 if dtype == "c128" else gc.TOL_F32_SHORT)
