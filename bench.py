@@ -428,6 +428,7 @@ def main():
             q = sop.Propagator(x.dims, x.spacing, 1, "c64")
             q.set_state(torch.from_numpy(x.psi0))
             q.set_potential(x.V)
+            q.autotune(x.dt, 8)   # launch shapes per lattice shape (cached); each size group uses its first member's
             props.append(q)
         bat = sop.Batch(props)
         fields = [x.field for x in ws]

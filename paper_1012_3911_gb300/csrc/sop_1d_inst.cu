@@ -94,6 +94,43 @@ template <typename Real, int N> int async_wp_of(int nc, bool contig) {
 }
 }  // namespace
 
+namespace {
+template <typename Real, int N, int VAR> int shape_wp(bool contig) {
+    if (contig) {
+        using Cfg = AsyncCfg<Real, N, 1, true, VAR>;
+        return Cfg::FITS ? Cfg::WP : 0;
+    }
+    using Cfg = AsyncCfg<Real, N, 1, false, VAR>;
+    return Cfg::FITS ? Cfg::WP : 0;
+}
+template <typename Real, int N> int shape_wp_of(int shape, bool contig) {
+    switch (shape) {
+        case 1: return shape_wp<Real, N, 1>(contig);
+        case 2: return shape_wp<Real, N, 2>(contig);
+        case 3: return shape_wp<Real, N, 3>(contig);
+        case 4: return shape_wp<Real, N, 4>(contig);
+        case 5: return shape_wp<Real, N, 5>(contig);
+        case 6: return shape_wp<Real, N, 6>(contig);
+        case 7: return shape_wp<Real, N, 7>(contig);
+        default: return shape_wp<Real, N, 0>(contig);
+    }
+}
+}  // namespace
+
+int async_pencils_per_cta_shape(bool f64, int n, bool contig, int shape) {
+    static_assert(kPassVariants == 8, "one case per launch shape");
+    if (shape != 0 && (f64 || !shape_sizes_has(n))) return 0;   // no kernel of that shape
+    switch (n) {
+#define SOP_CASE(N) \
+    case N:         \
+        return f64 ? shape_wp_of<double, N>(shape, contig) : shape_wp_of<float, N>(shape, contig);
+        SOP_SIZES(SOP_CASE)
+#undef SOP_CASE
+        default:
+            return 0;
+    }
+}
+
 int async_pencils_per_cta(bool f64, int n, int nc, bool contig) {
     switch (n) {
 #define SOP_CASE(N) \

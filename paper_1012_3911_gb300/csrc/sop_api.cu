@@ -1606,6 +1606,7 @@ struct sop_batch_s {
     // advances.  Captured once per descriptor buffer and replayed per step.
     cudaGraphExec_t step_exec = nullptr;
     const InstDesc *exec_desc = nullptr;
+    std::vector<int> exec_shapes;   // launch shapes of the groups the graph was captured with
     int exec_kernels = 0;
     std::vector<cudaStream_t> side;
     cudaStream_t cap = nullptr;   // capture stream
@@ -1634,37 +1635,46 @@ int batch_free(sop_batch b) {
 }
 
 // One multi-instance pass of a replayed step on stream st with its own counter.
-cudaError_t batch_launch_on(sop_batch b, PassArgs &a, bool contig, cudaStream_t st, unsigned long long *ctr) {
+cudaError_t batch_launch_shape(sop_batch b, PassArgs &a, bool contig, int shape, cudaStream_t st, int64_t *adv);
+
+cudaError_t batch_launch_on(sop_batch b, PassArgs &a, bool contig, cudaStream_t st, unsigned long long *ctr,
+                            int shape) {
     sop_plan p0 = b->plans[0];
     a.errflag = p0->errflag;
     a.wait_ns = p0->wait_ns;
     a.tile_ctr = ctr;
     a.tile_base[0] = a.tile_base[1] = 0;
     a.n_comp_total = 1;
-    TensorMapBytes tm;
-    std::memset(&tm, 0, sizeof(tm));
     int64_t adv = 0;
-    if (b->f64)
-        return contig ? launch_async_f64_contig(a, 1, tm, st, &adv) : launch_async_f64_strided(a, 1, tm, st, &adv);
-    return contig ? launch_async_f32_contig(a, 1, tm, st, &adv) : launch_async_f32_strided(a, 1, tm, st, &adv);
+    return batch_launch_shape(b, a, contig, shape, st, &adv);
 }
 
 // One multi-instance pass over the lattices of a group.
-int batch_launch(sop_batch b, PassArgs &a, bool contig, const char *what) {
+// shape: launch shape of the group (0: default); shapes without a kernel
+// for the size fall back to shape 0.
+cudaError_t batch_launch_shape(sop_batch b, PassArgs &a, bool contig, int shape, cudaStream_t st, int64_t *adv) {
+    TensorMapBytes tm;
+    std::memset(&tm, 0, sizeof(tm));
+    cudaError_t e = cudaErrorInvalidValue;
+    if (shape > 0 && shape < kPassVariants && !b->f64) {
+        e = launch_async_variant(false, contig, shape, a, 1, tm, st, adv);
+        if (e == cudaErrorInvalidValue) cudaGetLastError();
+    }
+    if (e != cudaErrorInvalidValue) return e;
+    if (b->f64)
+        return contig ? launch_async_f64_contig(a, 1, tm, st, adv) : launch_async_f64_strided(a, 1, tm, st, adv);
+    return contig ? launch_async_f32_contig(a, 1, tm, st, adv) : launch_async_f32_strided(a, 1, tm, st, adv);
+}
+
+int batch_launch(sop_batch b, PassArgs &a, bool contig, const char *what, int shape = 0) {
     sop_plan p0 = b->plans[0];
     a.errflag = p0->errflag;
     a.wait_ns = p0->wait_ns;
     a.tile_ctr = b->tile_ctr;
     a.tile_base[0] = a.tile_base[1] = b->tile_base;
     a.n_comp_total = 1;
-    TensorMapBytes tm;
-    std::memset(&tm, 0, sizeof(tm));
     int64_t adv = 0;
-    cudaError_t e;
-    if (b->f64)
-        e = contig ? launch_async_f64_contig(a, 1, tm, b->stream, &adv) : launch_async_f64_strided(a, 1, tm, b->stream, &adv);
-    else
-        e = contig ? launch_async_f32_contig(a, 1, tm, b->stream, &adv) : launch_async_f32_strided(a, 1, tm, b->stream, &adv);
+    cudaError_t e = batch_launch_shape(b, a, contig, shape, b->stream, &adv);
     if (e != cudaSuccess) return cuda_fail(e, what);
     b->tile_base += (unsigned long long)adv;
     p0->launches += 1;
@@ -1738,6 +1748,7 @@ int sop_batch_step(sop_batch b, int64_t n, double dt, const double *const *field
     struct Group {
         int axis;
         bool multi = false;   // one multi-instance launch (else one-shot passes per lattice)
+        int shape = 0;        // launch shape: the first member's (sop_autotune / sop_set_pass_shape)
         std::vector<int> members;
         int64_t first = 0, tiles = 0;
     };
@@ -1754,7 +1765,15 @@ int sop_batch_step(sop_batch b, int64_t n, double dt, const double *const *field
             Group &g = kv.second;
             g.first = (int64_t)hd.size();
             const int axis = g.axis;
-            const int wp = async_pencils_per_cta(b->f64, (int)kv.first, 1, axis == 0);
+            g.shape = b->plans[g.members[0]]->pass_var[axis == 0 ? 0 : 1][0];
+            if (b->f64) g.shape = 0;   // shapes other than 0 exist for complex64 only
+            // pencils per CTA of the group's launch shape: the tiles of every
+            // lattice are laid out for it
+            int wp = async_pencils_per_cta_shape(b->f64, (int)kv.first, axis == 0, g.shape);
+            if (wp <= 0) {
+                g.shape = 0;
+                wp = async_pencils_per_cta(b->f64, (int)kv.first, 1, axis == 0);
+            }
             g.multi = wp > 0 && b->plans[g.members[0]]->async_passes;
             if (!g.multi) continue;
             int64_t tiles = 0;
@@ -1853,7 +1872,8 @@ int sop_batch_step(sop_batch b, int64_t n, double dt, const double *const *field
             a.p_table0 = P0;
             a.n_total = n;
             a.n_tiles = g.tiles;
-            if ((rc2 = batch_launch(b, a, true, "batched real-space pass"))) return rc2;
+            a.stw = p0->stw[0][0];   // per-stage twiddles of this x size (shapes reading them through L1)
+            if ((rc2 = batch_launch(b, a, true, "batched real-space pass", g.shape))) return rc2;
         }
         if (P == n) return SOP_OK;
         for (auto &kv : gy) {
@@ -1875,7 +1895,8 @@ int sop_batch_step(sop_batch b, int64_t n, double dt, const double *const *field
             a.p_table0 = P0;
             a.n_total = n;
             a.n_tiles = g.tiles;
-            if ((rc2 = batch_launch(b, a, false, "batched momentum-space pass"))) return rc2;
+            a.stw = p0->stw[1][0];
+            if ((rc2 = batch_launch(b, a, false, "batched momentum-space pass", g.shape))) return rc2;
         }
         return SOP_OK;
     };
@@ -1887,8 +1908,11 @@ int sop_batch_step(sop_batch b, int64_t n, double dt, const double *const *field
     for (auto *gm : {&gx, &gy})
         for (auto &kv : *gm) all_multi = all_multi && kv.second.multi;
     const size_t ngroups = gx.size() + gy.size();
+    std::vector<int> shapes_now;
+    for (auto *gm : {&gx, &gy})
+        for (auto &kv : *gm) shapes_now.push_back(kv.second.shape);
     auto ensure_graph = [&]() -> int {
-        if (b->step_exec && b->exec_desc == b->desc) return SOP_OK;
+        if (b->step_exec && b->exec_desc == b->desc && b->exec_shapes == shapes_now) return SOP_OK;
         if (b->step_exec) {
             cudaGraphExecDestroy(b->step_exec);
             b->step_exec = nullptr;
@@ -1945,7 +1969,8 @@ int sop_batch_step(sop_batch b, int64_t n, double dt, const double *const *field
                 a.n_total = n;
                 a.n_tiles = g.tiles;
                 a.row_dev = b->row_dev;
-                if (e2 == cudaSuccess) e2 = batch_launch_on(b, a, contig, st, b->gctr + 2 * (ctr0 + k));
+                a.stw = p0->stw[contig ? 0 : 1][0];
+                if (e2 == cudaSuccess) e2 = batch_launch_on(b, a, contig, st, b->gctr + 2 * (ctr0 + k), g.shape);
                 ++kernels;
                 cudaEvent_t join = b->evs[2 + 2 * k + (contig ? 0 : 1)];
                 if (e2 == cudaSuccess) e2 = cudaEventRecord(join, st);
@@ -1968,6 +1993,7 @@ int sop_batch_step(sop_batch b, int64_t n, double dt, const double *const *field
             return cuda_fail(e, "capturing the batched step graph");
         }
         b->exec_desc = b->desc;
+        b->exec_shapes = shapes_now;
         b->exec_kernels = kernels + 1;
         return SOP_OK;
     };

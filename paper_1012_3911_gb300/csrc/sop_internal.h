@@ -236,6 +236,17 @@ int stage_table_f64(int n, int nc, void *out, const void *tw, cudaStream_t s);
 // Pencils per CTA of the asynchronous pass (the tensor-map box width for
 // strided axes); 0 when that pass does not fit on an SM (one-shot passes).
 int async_pencils_per_cta(bool f64, int n, int nc, bool contig);
+// The same for one-component passes of launch shape `shape` (the pencils per
+// CTA of the contiguous axis depend on the shape; those of strided axes,
+// which set the tensor-map box, do not).
+int async_pencils_per_cta_shape(bool f64, int n, bool contig, int shape);
+// Sides with launch shapes other than 0 (sop_pass_var.cu instantiates these).
+#define SOP_VAR_SIZES(X) X(256) X(384) X(512) X(768) X(1024) X(1536) X(2048)
+inline bool shape_sizes_has(int64_t n) {
+#define SOP_VAR_HAS(N) n == N ||
+    return SOP_VAR_SIZES(SOP_VAR_HAS) false;
+#undef SOP_VAR_HAS
+}
 cudaError_t launch_1d_f32(const Args1D &a, int n, cudaStream_t s);
 cudaError_t launch_1d_f64(const Args1D &a, int n, cudaStream_t s);
 // Threads and dynamic shared memory of the pass kernel for (dtype, n, nc, contig).

@@ -27,7 +27,6 @@
 #define SOP_SUFFIX_double _f64
 #define SOP_VAR_NAME SOP_CAT(SOP_CAT(SOP_CAT(launch_async_var, SOP_CAT(SOP_SUFFIX_, SOP_REAL)), SOP_KIND), SOP_VAR)
 
-#define SOP_VAR_SIZES(X) X(256) X(384) X(512) X(768) X(1024) X(1536) X(2048)
 
 namespace sop {
 

@@ -117,3 +117,29 @@ def test_replayed_step_graph_equals_direct_launches(n, monkeypatch):
             p.close()
     for g, d in zip(out["1"], out["0"]):
         assert torch.equal(g, d)
+
+
+@pytest.mark.parametrize("shapes", [(3, 2), (7, 3), (1, 5), (2, 0), (6, 4)])
+def test_batch_with_launch_shapes_equals_separate_steps(shapes):
+    """Member plans with launch shapes set (as sop_autotune leaves them): the
+    batch launches each size group with its first member's shapes and stays
+    bit-identical to stepping every plan alone with its own shapes."""
+    import torch
+    n = 12
+    sides = SIDES + [(192, 256), (256, 96)]   # sides without shapes other than 0 fall back to shape 0
+    ws = [wl.config5_instance(k, sides=s, n_steps=n) for k, s in enumerate(sides)]
+    alone = _props(ws, "c64")
+    together = _props(ws, "c64")
+    for p in alone + together:
+        p.set_pass_shape(0, shapes[0])
+        p.set_pass_shape(1, shapes[1])
+    for p, w in zip(alone, ws):
+        p.step(n, w.dt, w.field)
+    b = sop.Batch(together)
+    b.step(n, ws[0].dt, [w.field for w in ws])
+    torch.cuda.synchronize()
+    for a, c in zip(alone, together):
+        assert torch.equal(a.state, c.state)
+    b.close()
+    for p in alone + together:
+        p.close()
