@@ -180,6 +180,10 @@ def config_legs(args, sop, wl, torch, stream, flush, peak):
     q.close()
 
     flops = fp64_flop_counts()
+    # B_min per point and step (two round trips of psi plus FP32 V) and the
+    # bytes the pass design moves (every pass reads and writes psi; the
+    # real-space pass reads the 8-byte complex phase table)
+    design_pt = {4: 2 * 2 * 32 + 8, 3: 4 * 2 * 8 + 8, 2: 2 * 2 * 8 + 8}
     for cfg, make, b_per_pt in ((4, wl.config4, 4 * 32 + 4), (3, wl.config3, 4 * 8 + 4), (2, wl.config2, 4 * 8 + 4)):
         w = make()
         g = golden_sample(cfg)
@@ -191,9 +195,12 @@ def config_legs(args, sop, wl, torch, stream, flush, peak):
                    "pass_shapes": shapes}
             if dtype == "c64":
                 bmin = b_per_pt * w.npoints
+                dsg = design_pt[cfg] * w.npoints
                 ent["roofline"] = {"bound": "hbm", "step_b_min_bytes": bmin,
                                    "achieved": bmin / (t / w.n_steps) / 1e9, "peak": peak, "unit": "GB/s",
-                                   "frac": bmin / (t / w.n_steps) / 1e9 / peak}
+                                   "frac": bmin / (t / w.n_steps) / 1e9 / peak,
+                                   "design_bytes_per_step": dsg,
+                                   "design_frac": dsg / (t / w.n_steps) / 1e9 / peak}
             elif flops is not None and cfg in (2, 4):
                 key_f = {2: "schrodinger_2d", 4: "dirac_2d"}[cfg]
                 fpp = flops.get("flops_per_point_step", {}).get(key_f)
