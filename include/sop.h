@@ -106,7 +106,10 @@ int sop_bind_state(sop_plan plan, void *psi_dev);
  * term) from a device array of prod(dims) reals, FP64 if v_is_fp64 else
  * FP32.  The plan copies it (FP64) and rebuilds the phase tables
  * exp(-i V tau/(2 hbar)) and exp(-i V tau/hbar) at the next sop_step.
- * A plan whose potential was never set uses V = 0. */
+ * A plan whose potential was never set uses V = 0.  The conversion checks
+ * every value and the call synchronises the plan stream to read the check:
+ * SOP_EINVAL for a value that is not finite (the plan is then left without a
+ * potential), SOP_EINVAL for a NULL or misaligned pointer. */
 int sop_set_potential(sop_plan plan, const void *V_dev, int v_is_fp64);
 
 /* Meaning of the field samples of a Schroedinger plan (Sec. 2.2):
@@ -199,7 +202,10 @@ int64_t sop_launch_counter(sop_plan plan);
  * the bound state (allocated like sop_energy's scratch if absent), so the
  * state is unchanged.  Results are cached per process for the lattice shape,
  * component count, dtype and device: a later plan of the same shape takes
- * them without timing.  chosen (may be NULL) receives 2 ints: the shapes of
+ * them without timing; with the environment variable SOP_AUTOTUNE_CACHE
+ * naming a file, choices are also read from it (lines for this device model)
+ * and new ones appended, so they persist across processes.  chosen (may be
+ * NULL) receives 2 ints: the shapes of
  * the contiguous and the strided passes.  Synchronises the plan stream.
  * One-dimensional plans have no pencil passes (chosen = {0, 0}).
  * Errors: SOP_EINVAL (null plan), SOP_ESTATE (no state bound), SOP_ECUDA,
@@ -226,6 +232,13 @@ int sop_set_pass_shape(sop_plan plan, int axis_kind, int shape);
  * still complete normally, which is how the error path is tested.
  * SOP_EINVAL for a null plan. */
 int sop_set_wait_limit(sop_plan plan, uint64_t wait_ns);
+
+/* Allocation-failure injection for tests of the error paths (not part of the
+ * paper's method): after `after` more successful device allocations by this
+ * library, the next one fails as if the device were out of memory (the call
+ * that needed it returns SOP_ENOMEM and releases what it had allocated); a
+ * negative value turns the injection off.  Process-wide.  Returns SOP_OK. */
+int sop_debug_fail_alloc(int64_t after);
 
 /* Measured FMA throughput of the current device (not part of the paper's
  * method: the denominator of the arithmetic roofline reported for the FP64

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <mutex>
 #include <cmath>
@@ -25,6 +26,7 @@
 #include <cstring>
 #include <string>
 #include <map>
+#include <set>
 #include <vector>
 
 #include "sop.h"
@@ -111,6 +113,7 @@ struct sop_plan_s {
 
     void *psi = nullptr;
     double *V = nullptr;
+    int *vbad = nullptr;            // set by the potential conversion for a non-finite value
     bool v_set = false;
     sop_plan rev = nullptr;         // same lattice, stepped with -dt (costates of sop_adjoint_gradient)
 
@@ -173,8 +176,16 @@ namespace {
 
 bool is_finite(double x) { return std::isfinite(x); }
 
+// Allocation-failure injection (sop_debug_fail_alloc): the number of
+// device allocations still to succeed before one fails, or -1 (off).
+std::atomic<int64_t> g_fail_alloc{-1};
+
 template <typename T> int dalloc(T **p, size_t bytes, const char *what) {
     if (bytes == 0) bytes = 16;
+    if (g_fail_alloc.load() >= 0 && g_fail_alloc.fetch_sub(1) == 0) {
+        *p = nullptr;
+        return fail(SOP_ENOMEM, std::string("cudaMalloc(") + what + "): injected allocation failure");
+    }
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -282,6 +293,7 @@ int plan_free(sop_plan p) {
     dfree(p->theta);
     dfree(p->ftab);
     dfree(p->ftab_h);
+    dfree(p->vbad);
     dfree(p->fvh);
     dfree(p->fvec);
     dfree(p->partial);
@@ -1350,11 +1362,22 @@ int sop_set_potential(sop_plan p, const void *V_dev, int v_is_fp64) {
     if (!p->V) rc = dalloc(&p->V, (size_t)p->npts * sizeof(double), "potential");
     if (!rc && !p->vhalf) rc = dalloc(&p->vhalf, (size_t)p->npts * p->csz, "half phase table");
     if (!rc && !p->vfull) rc = dalloc(&p->vfull, (size_t)p->npts * p->csz, "full phase table");
+    if (!rc && !p->vbad) rc = dalloc(&p->vbad, sizeof(int), "potential check");
     if (rc) return rc;
     Bracket br(p, 4);
-    cudaError_t e = convert_potential(p->V, V_dev, p->npts, v_is_fp64 != 0, p->stream);
+    cudaError_t e = cudaMemsetAsync(p->vbad, 0, sizeof(int), p->stream);
+    if (e == cudaSuccess) e = convert_potential(p->V, V_dev, p->npts, v_is_fp64 != 0, p->vbad, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "convert_potential");
     br.done();
+    int bad = 0;
+    e = cudaMemcpyAsync(&bad, p->vbad, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sop_set_potential: reading the potential check");
+    if (bad) {
+        p->v_set = false;
+        p->tables_valid = false;
+        return fail(SOP_EINVAL, "sop_set_potential: V holds a value that is not finite (NaN or Inf)");
+    }
     p->v_set = true;
     p->tables_valid = false;
     return SOP_OK;
@@ -1480,6 +1503,11 @@ int sop_profile_read(sop_plan p, double *ms, int64_t *launches, int max_classes)
 
 int64_t sop_launch_counter(sop_plan p) { return p ? p->launches : 0; }
 
+int sop_debug_fail_alloc(int64_t after) {
+    g_fail_alloc.store(after < 0 ? -1 : after);
+    return SOP_OK;
+}
+
 int sop_set_wait_limit(sop_plan p, uint64_t wait_ns) {
     if (!p) return fail(SOP_EINVAL, "sop_set_wait_limit: null plan");
     p->wait_ns = wait_ns;
@@ -1506,8 +1534,34 @@ int sop_autotune(sop_plan p, double dt, int trial_steps, int *chosen) {
     static std::mutex mu;
     static std::map<std::vector<int64_t>, std::pair<int, int>> cache;
     const std::vector<int64_t> key = {p->device, p->ndim, p->dims[0], p->dims[1], p->dims[2], p->comps, p->f64 ? 1 : 0};
+    // SOP_AUTOTUNE_CACHE=<file>: choices persist across processes, one line
+    // per device model and shape ("<model> ndim n0 n1 n2 comps f64 C S")
+    const char *cache_file = std::getenv("SOP_AUTOTUNE_CACHE");
+    std::string model;
+    if (cache_file && *cache_file) {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) model = prop.name;
+        for (char &ch : model)
+            if (ch == ' ') ch = '_';
+    }
     {
         std::lock_guard<std::mutex> lock(mu);
+        static std::set<std::string> loaded;   // (file, device) pairs read once
+        const std::string once = model.empty() ? std::string() : std::string(cache_file) + "#" + std::to_string(p->device);
+        if (!model.empty() && !loaded.count(once)) {
+            loaded.insert(once);
+            if (FILE *f = std::fopen(cache_file, "r")) {
+                char name[256];
+                long long v[7];
+                int c0, c1;
+                while (std::fscanf(f, "%255s %lld %lld %lld %lld %lld %lld %d %d", name, &v[0], &v[1], &v[2], &v[3],
+                                   &v[4], &v[5], &c0, &c1) == 9)
+                    if (model == name && c0 >= 0 && c0 < kPassVariants && c1 >= 0 && c1 < kPassVariants &&
+                        (v[5] == 0 || (c0 == 0 && c1 == 0)))   // complex128 has shape 0 only
+                        cache[{p->device, v[0], v[1], v[2], v[3], v[4], v[5]}] = {c0, c1};
+                std::fclose(f);
+            }
+        }
         auto it = cache.find(key);
         if (it != cache.end()) {
             p->pass_var[0][0] = p->pass_var[0][1] = it->second.first;
@@ -1576,6 +1630,12 @@ int sop_autotune(sop_plan p, double dt, int trial_steps, int *chosen) {
     {
         std::lock_guard<std::mutex> lock(mu);
         cache[key] = {best[0], best[1]};
+        if (!model.empty())
+            if (FILE *f = std::fopen(cache_file, "a")) {
+                std::fprintf(f, "%s %d %lld %lld %lld %d %d %d %d\n", model.c_str(), p->ndim, (long long)p->dims[0],
+                             (long long)p->dims[1], (long long)p->dims[2], p->comps, p->f64 ? 1 : 0, best[0], best[1]);
+                std::fclose(f);
+            }
     }
     if (chosen) {
         chosen[0] = best[0];

@@ -275,7 +275,8 @@ cudaError_t build_field_tables(void *out, const double *fvec, int64_t n_rows, in
                                const int64_t *offsets, int64_t row_len, bool f64, cudaStream_t s);
 cudaError_t build_dirac_table(void *out, const int64_t *dims, const double *spacing, double mass,
                               double c, double hbar, double dt, bool f64, cudaStream_t s);
-cudaError_t convert_potential(double *out, const void *in, int64_t n, bool in_f64, cudaStream_t s);
+// out = in in FP64; *bad (if not null) becomes nonzero for a non-finite value.
+cudaError_t convert_potential(double *out, const void *in, int64_t n, bool in_f64, int *bad, cudaStream_t s);
 
 // Reductions (sop_reduce.cu).  partial must hold reduce_blocks() doubles.
 int reduce_blocks();

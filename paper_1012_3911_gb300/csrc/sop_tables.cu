@@ -137,10 +137,16 @@ __global__ void k_dirac(void *out, int64_t nx, int64_t ny, double hx, double hy,
     }
 }
 
-__global__ void k_convert(double *out, const void *in, int64_t n, bool in_f64) {
+// out = in in FP64; *bad becomes nonzero if any value is not finite.
+__global__ void k_convert(double *out, const void *in, int64_t n, bool in_f64, int *bad) {
+    bool ok = true;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (int64_t)gridDim.x * blockDim.x)
-        out[j] = in_f64 ? reinterpret_cast<const double *>(in)[j] : (double)reinterpret_cast<const float *>(in)[j];
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double v = in_f64 ? reinterpret_cast<const double *>(in)[j] : (double)reinterpret_cast<const float *>(in)[j];
+        out[j] = v;
+        ok = ok && isfinite(v);
+    }
+    if (!__all_sync(0xffffffffu, ok) && (threadIdx.x & 31) == 0 && bad) atomicOr(bad, 1);
 }
 
 unsigned grid_for(int64_t n, int block) {
@@ -205,8 +211,8 @@ cudaError_t build_dirac_table(void *out, const int64_t *dims, const double *spac
     return cudaGetLastError();
 }
 
-cudaError_t convert_potential(double *out, const void *in, int64_t n, bool in_f64, cudaStream_t s) {
-    k_convert<<<grid_for(n, 256), 256, 0, s>>>(out, in, n, in_f64);
+cudaError_t convert_potential(double *out, const void *in, int64_t n, bool in_f64, int *bad, cudaStream_t s) {
+    k_convert<<<grid_for(n, 256), 256, 0, s>>>(out, in, n, in_f64, bad);
     return cudaGetLastError();
 }
 

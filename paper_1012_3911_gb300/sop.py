@@ -238,6 +238,15 @@ def sop_fma_peak(f64: bool = True, stream=None) -> float:
     return out.value
 
 
+def sop_debug_fail_alloc(after: int) -> None:
+    """Make the device allocation after `after` more successful ones fail (-1: off)."""
+    lib = load()
+    fn = lib.sop_debug_fail_alloc
+    fn.argtypes = [ctypes.c_int64]
+    fn.restype = ctypes.c_int
+    _check(fn(int(after)))
+
+
 def sop_set_wait_limit(plan: int, wait_ns: int) -> None:
     """Limit of the pass kernels' tile-copy waits in ns (0: the default 2 s)."""
     lib = load()

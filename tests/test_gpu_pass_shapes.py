@@ -72,3 +72,31 @@ def test_autotune_keeps_the_state_and_matches_the_oracle(dtype):
     err = gc.relerr(prop.state.cpu().numpy(), ref)
     prop.close()
     assert err < (gc.TOL_F64 if dtype == "c128" else gc.TOL_F32_SHORT), err
+
+
+def test_autotune_cache_file_is_read_and_appended(tmp_path, monkeypatch):
+    """SOP_AUTOTUNE_CACHE: a line for this device model and lattice shape is
+    taken without timing; a shape tuned afresh is appended to the file."""
+    model = torch.cuda.get_device_name(0).replace(" ", "_")
+    path = tmp_path / "shapes.txt"
+    # 2D 192 x 96 complex64 (sides no other test tunes) -> shapes 3 and 5;
+    # a complex128 line with shapes other than 0 is ignored
+    path.write_text(f"{model} 2 192 96 1 1 0 3 5\n{model} 2 192 96 1 1 1 4 4\nother_gpu 2 96 192 1 1 0 2 2\n")
+    monkeypatch.setenv("SOP_AUTOTUNE_CACHE", str(path))
+    w = gc.random_workload((192, 96), 1, seed=5, n_steps=2, dt=0.01, field_scale=0.05)
+    prop = sop.Propagator(w.dims, w.spacing, 1, "c64")
+    prop.set_state(torch.from_numpy(w.psi0))
+    assert prop.autotune(w.dt, 2) == [3, 5]
+    prop.close()
+    prop = sop.Propagator(w.dims, w.spacing, 1, "c128")
+    prop.set_state(torch.from_numpy(w.psi0))
+    assert prop.autotune(w.dt, 2) == [0, 0]   # tuned: the bad line was not taken
+    prop.close()
+    w2 = gc.random_workload((96, 192), 1, seed=6, n_steps=2, dt=0.01, field_scale=0.05)
+    prop = sop.Propagator(w2.dims, w2.spacing, 1, "c64")
+    prop.set_state(torch.from_numpy(w2.psi0))
+    chosen = prop.autotune(w2.dt, 2)
+    prop.close()
+    lines = path.read_text().split("\n")
+    assert f"{model} 2 96 192 1 1 0 {chosen[0]} {chosen[1]}" in lines
+    assert f"{model} 2 192 96 1 1 1 0 0" in lines
