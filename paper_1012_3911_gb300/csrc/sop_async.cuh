@@ -224,10 +224,22 @@ template <> struct PassPolicy<7> : PolBase {
 };
 static_assert(kPassVariants == 8, "one PassPolicy per variant");
 
+// Values per thread of the persistent passes where they differ from the
+// Geometry default (0: the default).  Complex64 component pairs on power-of-
+// two sides >= 512 hold 16 values per component instead of 8: 1024 points
+// then take 16·16·4 (two exchanges per transform) instead of 8·8·8·2 (three),
+// and the two-exchange transform wins despite the doubled register set
+// (measured on GB300, 1024^2 Dirac pairs: 62.5 -> 56.2 us per split step
+// with the default shapes).  Complex128 pairs would spill and keep 8.
+template <typename Real, int N, int NC> constexpr int pass_ev() {
+    return (sizeof(Real) == 4 && NC == 2 && N >= 512 && (N & (N - 1)) == 0) ? 16 : 0;
+}
+
 template <typename Real, int N, int NC, bool CONTIG, int VAR = 0> struct AsyncCfg {
     using Pol = PassPolicy<VAR>;
+    static constexpr int EV0 = pass_ev<Real, N, NC>();
     // 32 values per thread only where the size's default is 16
-    static constexpr int EV = (Pol::E > 0 && Geometry<N, NC>::E == 16 && N >= 512) ? Pol::E : 0;
+    static constexpr int EV = (Pol::E > 0 && Geometry<N, NC, EV0>::E == 16 && N >= 512) ? Pol::E : EV0;
     using G = Geometry<N, NC, EV>;
     using C = cplx_t<Real>;
     static constexpr int E = G::E;
@@ -295,6 +307,7 @@ template <typename Real, int N, int NC, bool CONTIG, int VAR = 0> struct AsyncCf
     static constexpr int ctas_for(size_t bytes) { return (int)((228 * 1024) / (bytes + 1024)); }
     static constexpr bool LEAN = Pol::L1TAB || (SOP_LEAN_TABLES != 0 && CSZ == 8 && NC == 2 && !CONTIG &&
                                                 ctas_for(OFF_BUF + NBUF * BUF) > ctas_for(OFF_AXT + AXT));
+    static_assert(!LEAN || EV == EV0, "the global stage table is laid out for the default values per thread");
     static constexpr bool AXL1 = LEAN || Pol::AXL1;   // pass-axis row through L1
     static constexpr size_t SMEM = LEAN ? OFF_BUF + NBUF * BUF : (AXL1 ? OFF_AXT : OFF_AXT + AXT);
     // buffer and mbarrier phase parity of iteration it
@@ -312,7 +325,8 @@ template <typename Real, int N, int NC, bool CONTIG, int VAR = 0> struct AsyncCf
     static constexpr int minb() {
         int b = (int)((227 * 1024) / (SMEM > 0 ? SMEM : 1));
         const int bt = 2048 / THREADS;
-        const int regs = VAR == 0 ? (NC == 4 ? 128 : (LEAN ? 64 : 104)) : Pol::REGS;
+        int regs = VAR == 0 ? (NC == 4 ? 128 : (LEAN ? 64 : 104)) : Pol::REGS;
+        if (EV0 == 16 && NC == 2 && regs < 128) regs = 128;   // 32 values per thread: budgets below spill
         const int br = 65536 / (THREADS * regs);   // registers per thread to leave
         if (bt < b) b = bt;
         if (br < b) b = br;
@@ -900,14 +914,14 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
 template <typename Real, int N, int NC>
 __global__ void stage_table_kernel(void *out, const void *tw) {
     using C = cplx_t<Real>;
-    StageTable<C, N, Geometry<N, NC>::E>::fill(reinterpret_cast<C *>(out), reinterpret_cast<const C *>(tw),
-                                               (int)threadIdx.x, (int)blockDim.x);
+    StageTable<C, N, Geometry<N, NC, pass_ev<Real, N, NC>()>::E>::fill(
+        reinterpret_cast<C *>(out), reinterpret_cast<const C *>(tw), (int)threadIdx.x, (int)blockDim.x);
 }
 
 // out == nullptr: the number of entries; else fill out (async on s).
 template <typename Real, int N, int NC>
 int stage_table_t(void *out, const void *tw, cudaStream_t s) {
-    constexpr int entries = StageTable<cplx_t<Real>, N, Geometry<N, NC>::E>::ENTRIES;
+    constexpr int entries = StageTable<cplx_t<Real>, N, Geometry<N, NC, pass_ev<Real, N, NC>()>::E>::ENTRIES;
     if (out != nullptr && entries > 0) stage_table_kernel<Real, N, NC><<<1, 256, 0, s>>>(out, tw);
     return entries;
 }
