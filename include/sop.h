@@ -294,9 +294,12 @@ int sop_norm_noalloc(const void *psi_dev, int64_t n_values, int dtype, double sc
  * aligned.  field may be NULL (all zero).  Schroedinger plans with fewer
  * than 2^31 lattice points only (SOP_EUNSUPPORTED otherwise); SOP_ESTATE without a bound state; SOP_EINVAL
  * for n_steps < 1, every < 1, dt zero or not finite, non-finite samples or
- * bad pointers.  Allocates its checkpoints (ceil(n_steps/every) + every + 2
- * states) for the call and a second plan for the -dt steps on first use;
- * synchronises the plan stream. */
+ * bad pointers.  Its checkpoints (ceil(n_steps/every) + 2 every + 3 states
+ * and per-step overlaps) live in one device block that the plan keeps for
+ * later calls of the same or a smaller size (grown when a call needs more,
+ * freed by sop_plan_destroy); a second plan for the -dt steps is made on
+ * first use and takes this plan's launch shapes and potential; synchronises
+ * the plan stream. */
 int sop_adjoint_gradient(sop_plan plan, const void *phi_dev, int64_t n_steps, double dt,
                          const double *field_samples, int64_t every, double *J, double *grad_field,
                          double *grad_V_dev);

@@ -185,7 +185,8 @@ __global__ void __launch_bounds__(kThreads) k_accum(const C *a, const C *b, int6
 // partial[(k gridDim.x + block) 8 + v]; every point adds
 // sum_k w_k conj(lam_k) psi_k to its accumulator once (w = 1 for step 0,
 // else 2), instead of once per step.
-constexpr int kSegPts = 4;   // points per thread and chunk
+constexpr int kSegPts = 2;          // points per thread and chunk
+constexpr int kSegGrid = 152 * 8;   // blocks at most (one chunk each where the lattice allows)
 
 template <typename C>
 __global__ void __launch_bounds__(kThreads) k_seg_reduce(const C *__restrict__ lam, const C *__restrict__ psi,
@@ -222,8 +223,29 @@ __global__ void __launch_bounds__(kThreads) k_seg_reduce(const C *__restrict__ l
                 }
             }
         }
+        // slot k + 1 is fetched before slot k's block sums, so its load
+        // latency overlaps the shuffles
+        C un[kSegPts], vn[kSegPts];
+        auto fetch = [&](int k) {
+#pragma unroll
+            for (int q = 0; q < kSegPts; ++q) {
+                const int64_t j = base + threadIdx.x + (int64_t)q * kThreads;
+                if (j < npts) {
+                    un[q] = lam[(int64_t)k * npts + j];
+                    vn[q] = psi[(int64_t)k * npts + j];
+                }
+            }
+        };
+        fetch(0);
         for (int k = 0; k < count; ++k) {
             const R w = (m0 + k == 0) ? R(1) : R(2);
+            C uc[kSegPts], vc[kSegPts];
+#pragma unroll
+            for (int q = 0; q < kSegPts; ++q) {
+                uc[q] = un[q];
+                vc[q] = vn[q];
+            }
+            if (k + 1 < count) fetch(k + 1);
             R loc[kVals];
 #pragma unroll
             for (int v = 0; v < kVals; ++v) loc[v] = R(0);
@@ -231,7 +253,7 @@ __global__ void __launch_bounds__(kThreads) k_seg_reduce(const C *__restrict__ l
             for (int q = 0; q < kSegPts; ++q) {
                 const int64_t j = base + threadIdx.x + (int64_t)q * kThreads;
                 if (j < npts) {
-                    const C u = lam[(int64_t)k * npts + j], vv = psi[(int64_t)k * npts + j];
+                    const C u = uc[q], vv = vc[q];
                     const R re = u.x * vv.x + u.y * vv.y;   // conj(u) v
                     const R im = u.x * vv.y - u.y * vv.x;
                     ax_[q].add(w * re);
@@ -534,7 +556,7 @@ cudaError_t launch_inner(const void *a, const void *b, bool f64, int ndim, const
 
 constexpr int kSegMax = 64;   // slots per k_seg_reduce launch (shared memory: 512 B per slot)
 
-int seg_partials(int count) { return (count < kSegMax ? count : kSegMax) * kBlocks * kVals; }
+int seg_partials(int count) { return (count < kSegMax ? count : kSegMax) * kSegGrid * kVals; }
 
 cudaError_t launch_seg_reduce(const void *lam, const void *psi, bool f64, int count, int64_t m0, int ndim,
                               const int64_t *dims, const double *h, double dV, double *acc, double *partial,
@@ -549,18 +571,20 @@ cudaError_t launch_seg_reduce(const void *lam, const void *psi, bool f64, int co
         npts *= g.dims[ax];
     }
     double2 *ac = reinterpret_cast<double2 *>(acc);
+    const int64_t chunks = (npts + (int64_t)kThreads * kSegPts - 1) / ((int64_t)kThreads * kSegPts);
+    const int nb = (int)(chunks < kSegGrid ? chunks : kSegGrid);
     for (int k0 = 0; k0 < count; k0 += kSegMax) {
         const int c = count - k0 < kSegMax ? count - k0 : kSegMax;
         const size_t smem = (size_t)(kThreads / 32) * c * kVals * sizeof(double);
         if (f64)
-            k_seg_reduce<double2><<<kBlocks, kThreads, smem, s>>>(static_cast<const double2 *>(lam) + k0 * npts,
-                                                                  static_cast<const double2 *>(psi) + k0 * npts,
-                                                                  npts, c, m0 + k0, g, ac, partial);
+            k_seg_reduce<double2><<<nb, kThreads, smem, s>>>(static_cast<const double2 *>(lam) + k0 * npts,
+                                                             static_cast<const double2 *>(psi) + k0 * npts, npts, c,
+                                                             m0 + k0, g, ac, partial);
         else
-            k_seg_reduce<float2><<<kBlocks, kThreads, smem, s>>>(static_cast<const float2 *>(lam) + k0 * npts,
-                                                                 static_cast<const float2 *>(psi) + k0 * npts,
-                                                                 npts, c, m0 + k0, g, ac, partial);
-        k_seg_final<<<c, 32 * kVals, 0, s>>>(partial, kBlocks, dV, out, m0 + k0);
+            k_seg_reduce<float2><<<nb, kThreads, smem, s>>>(static_cast<const float2 *>(lam) + k0 * npts,
+                                                            static_cast<const float2 *>(psi) + k0 * npts, npts, c,
+                                                            m0 + k0, g, ac, partial);
+        k_seg_final<<<c, 32 * kVals, 0, s>>>(partial, nb, dV, out, m0 + k0);
     }
     return cudaGetLastError();
 }

@@ -116,6 +116,10 @@ struct sop_plan_s {
     int *vbad = nullptr;            // set by the potential conversion for a non-finite value
     bool v_set = false;
     sop_plan rev = nullptr;         // same lattice, stepped with -dt (costates of sop_adjoint_gradient)
+    uint64_t v_version = 0;         // count of successful sop_set_potential calls
+    uint64_t rev_v_version = 0;     // the version rev's potential was copied from
+    char *adj = nullptr;            // sop_adjoint_gradient buffers, kept across calls
+    size_t adj_cap = 0;
 
     void *tw[3] = {nullptr, nullptr, nullptr};
     void *stw[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};   // per-stage tables, nc = 1, 2
@@ -300,6 +304,7 @@ int plan_free(sop_plan p) {
     dfree(p->result);
     dfree(p->pgrid);
     dfree(p->scratch);
+    dfree(p->adj);
     dfree(p->errflag);
     dfree(p->tile_ctr);
     if (p->host_stage) cudaFreeHost(p->host_stage);
@@ -1380,6 +1385,7 @@ int sop_set_potential(sop_plan p, const void *V_dev, int v_is_fp64) {
     }
     p->v_set = true;
     p->tables_valid = false;
+    ++p->v_version;
     return SOP_OK;
 }
 
@@ -2118,39 +2124,47 @@ int sop_adjoint_gradient(sop_plan p, const void *phi_dev, int64_t n_steps, doubl
         r->async_passes = p->async_passes;
         p->rev = r;
     }
-    if (p->v_set) {
+    // the costate plan takes this plan's launch shapes and, once per potential
+    // version, its potential
+    for (int k = 0; k < 2; ++k)
+        for (int c = 0; c < 2; ++c) p->rev->pass_var[k][c] = p->pass_var[k][c];
+    if (!p->v_set) {
+        p->rev->v_set = false;
+        p->rev->tables_valid = false;
+        p->rev_v_version = 0;
+    } else if (p->rev_v_version != p->v_version || !p->rev->v_set) {
         rc = sop_set_potential(p->rev, p->V, 1);
         if (rc) return rc;
+        p->rev_v_version = p->v_version;
     }
     const size_t sb = (size_t)p->npts * p->csz;
     const int64_t K = (N + every - 1) / every;           // checkpoints at 0, every, 2 every, ...
     const int64_t S = std::min<int64_t>(every, N) + 1;   // states of one recomputed segment
-    char *ck = nullptr, *seg = nullptr, *lam = nullptr, *lseg = nullptr;
-    double *sdev = nullptr, *cdev = nullptr, *acc = nullptr, *part = nullptr;
-    auto cleanup = [&]() {
-        cudaStreamSynchronize(p->stream);
-        dfree(ck);
-        dfree(seg);
-        dfree(lam);
-        dfree(lseg);
-        dfree(sdev);
-        dfree(cdev);
-        dfree(acc);
-        dfree(part);
-    };
-    rc = dalloc(&ck, (size_t)K * sb, "adjoint checkpoints");
-    if (!rc) rc = dalloc(&seg, (size_t)S * sb, "adjoint segment");
-    if (!rc) rc = dalloc(&lam, sb, "adjoint costate");
-    if (!rc) rc = dalloc(&lseg, (size_t)S * sb, "adjoint costate segment");
-    if (!rc) rc = dalloc(&sdev, (size_t)(N + 1) * 8 * sizeof(double), "adjoint overlaps");
-    if (!rc) rc = dalloc(&cdev, 8 * sizeof(double), "adjoint target overlap");
-    if (!rc) rc = dalloc(&acc, (size_t)p->npts * 2 * sizeof(double), "adjoint accumulator");
-    if (!rc) rc = dalloc(&part, (size_t)std::max(inner_partials(), seg_partials((int)std::min<int64_t>(every, N))) *
-                                    sizeof(double), "adjoint partials");
-    if (rc) {
-        cleanup();
-        return rc;
+    // one device block, carved into the buffers below (256-byte aligned) and
+    // kept in the plan for the next call of the same or a smaller size
+    const size_t npart = (size_t)std::max(inner_partials(), seg_partials((int)std::min<int64_t>(every, N)));
+    const size_t sizes[8] = {(size_t)K * sb, (size_t)S * sb, sb, (size_t)S * sb, (size_t)(N + 1) * 8 * sizeof(double),
+                             8 * sizeof(double), (size_t)p->npts * 2 * sizeof(double), npart * sizeof(double)};
+    size_t offs[8], total = 0;
+    for (int k = 0; k < 8; ++k) {
+        offs[k] = total;
+        total += (sizes[k] + 255) & ~size_t(255);
     }
+    if (p->adj_cap < total) {
+        cudaStreamSynchronize(p->stream);
+        dfree(p->adj);
+        p->adj = nullptr;
+        p->adj_cap = 0;
+        if ((rc = dalloc(&p->adj, total, "adjoint buffers"))) return rc;
+        p->adj_cap = total;
+    }
+    char *const ck = p->adj + offs[0], *const seg = p->adj + offs[1], *const lam = p->adj + offs[2],
+               *const lseg = p->adj + offs[3];
+    double *const sdev = reinterpret_cast<double *>(p->adj + offs[4]);
+    double *const cdev = reinterpret_cast<double *>(p->adj + offs[5]);
+    double *const acc = reinterpret_cast<double *>(p->adj + offs[6]);
+    double *const part = reinterpret_cast<double *>(p->adj + offs[7]);
+    auto cleanup = [&]() { cudaStreamSynchronize(p->stream); };
     void *const psi_user = p->psi;
     const double dV = p->h[0] * (nd > 1 ? p->h[1] : 1.0) * (nd > 2 ? p->h[2] : 1.0);
     const double *F = field;

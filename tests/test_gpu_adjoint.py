@@ -95,3 +95,36 @@ def test_adjoint_rejects_dirac_and_bad_arguments():
         with pytest.raises(sop.SopError):
             sop.sop_adjoint_gradient(q.plan, phi, n, dt, None, every, 2)
     q.close()
+
+
+def test_adjoint_reuses_its_buffers_and_follows_the_potential():
+    """Repeated calls on one plan (the checkpoint block kept between calls,
+    grown for a longer run, reused for a shorter one) give exactly the
+    results of a fresh plan, and a new potential reaches the -dt plan."""
+    import torch
+    w, phi = _small_case((64, 48), 30, 33)
+    p = sop.Propagator(w.dims, w.spacing, 1, "c64")
+    p.set_state(torch.from_numpy(w.psi0))
+    p.set_potential(w.V)
+    p.set_pass_shape(1, 3)   # a tuned shape: the -dt plan must take it too (bitwise the same)
+    gV = torch.zeros(w.psi0.shape, dtype=torch.float64, device="cuda")
+    short = p.adjoint_gradient(phi, 12, w.dt, w.field[:12], 5, gV)
+    gV_short = gV.clone()
+    long_ = p.adjoint_gradient(phi, 30, w.dt, w.field, 7, gV)
+    gV_long = gV.clone()
+    again = p.adjoint_gradient(phi, 12, w.dt, w.field[:12], 5, gV)
+    assert again[0] == short[0] and np.array_equal(again[1], short[1]) and torch.equal(gV, gV_short)
+    V2 = w.V * 0.5
+    p.set_potential(V2)
+    moved = p.adjoint_gradient(phi, 30, w.dt, w.field, 7, gV)
+    p.close()
+    fresh = sop.Propagator(w.dims, w.spacing, 1, "c64")
+    fresh.set_state(torch.from_numpy(w.psi0))
+    fresh.set_potential(V2)
+    gV2 = torch.zeros_like(gV)
+    ref = fresh.adjoint_gradient(phi, 30, w.dt, w.field, 7, gV2)
+    fresh.close()
+    assert moved[0] == ref[0] and np.array_equal(moved[1], ref[1]) and torch.equal(gV, gV2)
+    assert moved[0] != long_[0]
+    ref_long = oadj.schrodinger_adjoint(w.psi0, w.V, w.spacing, w.dt, 30, w.field, phi)
+    _check(long_[0], long_[1], gV_long.cpu().numpy(), ref_long, 1e-4)
