@@ -195,10 +195,12 @@ int64_t sop_launch_counter(sop_plan plan);
  * stage twiddles and the pass-axis factor row live (shared memory or L1) and
  * the register budget; SOP_PASS_SHAPES shapes exist, 0 is the default.
  *
- * sop_autotune: times every shape of the contiguous-axis pass (x) and then of
- * the strided-axis passes (y, z) for this plan's lattice, component count
- * and dtype, over trial_steps split steps of size dt (<= 0: 16) with no
- * field (best of three trials), and keeps the fastest of each.  The trials run on a scratch copy of
+ * sop_autotune: times every shape of the contiguous-axis pass (x), then of
+ * the strided-axis passes (y, z), then both again with the other kind's
+ * choice in place (two rounds of coordinate descent), for this plan's
+ * lattice, component count and dtype, over trial_steps split steps of size
+ * dt (<= 0: 16) with no field (best of five trials of whole steps), and
+ * keeps the fastest of each.  The trials run on a scratch copy of
  * the bound state (allocated like sop_energy's scratch if absent), so the
  * state is unchanged.  Results are cached per process for the lattice shape,
  * component count, dtype and device: a later plan of the same shape takes

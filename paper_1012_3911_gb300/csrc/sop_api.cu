@@ -1595,15 +1595,20 @@ int sop_autotune(sop_plan p, double dt, int trial_steps, int *chosen) {
     p->psi = p->scratch;
     p->prof_every = 0;
     int best[2] = {0, 0};
-    for (int kind = 0; kind < 2 && !rc; ++kind) {
+    // coordinate descent over the two pass kinds, twice (the step time of a
+    // shape depends on the other kind's shape through the launch overlap);
+    // each shape is timed as the best of five trials of whole split steps
+    for (int sweep = 0; sweep < 4 && !rc; ++sweep) {
+        const int kind = sweep & 1;
         float best_ms = 0.f;
         const int nshapes = p->f64 ? 1 : kPassVariants;   // shapes 1.. exist for complex64 only
+        if (nshapes == 1) continue;
         for (int v = 0; v < nshapes && !rc; ++v) {
             p->pass_var[kind][0] = p->pass_var[kind][1] = v;
             rc = step_impl(p, 2, dt, nullptr);   // warm-up (tables, tensor maps, attributes)
             if (rc) break;
             float ms = 0.f;
-            for (int rep = 0; rep < 3 && !rc; ++rep) {   // best of three trials
+            for (int rep = 0; rep < 5 && !rc; ++rep) {   // best of five trials
                 cudaEventRecord(e0, p->stream);
                 rc = step_impl(p, trial_steps, dt, nullptr);
                 if (rc) break;
@@ -1624,6 +1629,7 @@ int sop_autotune(sop_plan p, double dt, int trial_steps, int *chosen) {
         }
         p->pass_var[kind][0] = p->pass_var[kind][1] = best[kind];
     }
+    for (int kind = 0; kind < 2; ++kind) p->pass_var[kind][0] = p->pass_var[kind][1] = best[kind];
     p->psi = saved_psi;
     p->prof_every = saved_prof;
     cudaEventDestroy(e0);
