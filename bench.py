@@ -654,7 +654,8 @@ def main():
         tp = e0.elapsed_time(e1) * 1e-3
         dirac_profile = {"value": n4 * n4 * T4 / tp, "unit": UNIT, "dtype": "f32",
                          "workload": f"2D Dirac {n4}^2 (config-4 lattice and potential), A_y(x, t) of a pulse "
-                                     f"travelling along x, {T4} steps, per-column mixing as its own pass",
+                                     f"travelling along x, {T4} steps, per-column mixing inside the x pass of the "
+                                     f"component pairs",
                          "us_per_step": tp / T4 * 1e6, "uniform_A_us_per_step": tu / T4 * 1e6}
         qp.close()
         torch.cuda.empty_cache()

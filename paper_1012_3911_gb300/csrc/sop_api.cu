@@ -689,6 +689,36 @@ const void *profile_row(sop_plan p, int64_t P, int64_t P0) {
 int step_dirac2d_profile(sop_plan p, int64_t n, double dt) {
     const int64_t nx = p->dims[0];
     int rc = SOP_OK;
+    if (p->async_passes && async_pencils_per_cta(p->f64, (int)nx, 2, true) > 0) {
+        // A in the lattice plane keeps the component pairs (1,4) and (2,3)
+        // (b_3 = d_1 = d_2 = 0 in every merged mixing), so the per-column
+        // mixing runs inside the x pass of the pairs, as the uniform mixing
+        // does: two passes per step.
+        for (int64_t P0 = 0; P0 <= n; P0 += kProfileChunk) {
+            const int64_t P1 = std::min<int64_t>(n + 1, P0 + kProfileChunk);
+            if ((rc = profile_rows(p, n, dt, P0, P1))) return rc;
+            for (int64_t P = P0; P < P1; ++P) {
+                const bool smp = step_sampled(p, P);
+                PassArgs a;
+                base_args(p, a, p->psi, 0);
+                a.pre = P > 0 ? +1 : 0;
+                a.post = P < n ? -1 : 0;
+                a.op = OP_DV;
+                a.vtab = p->v_set ? ((P == 0 || P == n) ? p->vhalf : p->vfull) : nullptr;
+                a.rows4 = profile_row(p, P, P0);
+                if ((rc = run_pass(p, a, 2, 0, "Dirac real-space pass", smp))) return rc;
+                if (P == n) break;
+                PassArgs k;
+                base_args(p, k, p->psi, 1);
+                k.pre = -1;
+                k.post = +1;
+                k.op = OP_DT;
+                k.dtab = p->dtab;
+                if ((rc = run_pass(p, k, 2, 1, "Dirac momentum-space pass", smp))) return rc;
+            }
+        }
+        return SOP_OK;
+    }
     // ---- Dirac, 2D, column-dependent A: the mixing runs as its own
     // streaming pass between the x transforms of the four components;
     // the momentum-space factor stays fused in the y pass of the pairs.

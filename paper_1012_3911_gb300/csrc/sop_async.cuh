@@ -842,7 +842,33 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
         } else if constexpr (NC == 4) {
             apply_op4<Real, E, T>(v, a, base, stride, t, want_v ? vt : nullptr);
         } else {
-            if (a.op == OP_DV) {
+            if (a.op == OP_DV && a.rows4 != nullptr && CONTIG) {
+                // A varying along x_1 (in the lattice plane): per-column merged
+                // mixing a + i b.alpha + i d.Sigma with b_3 = d_1 = d_2 = 0, which
+                // keeps the pairs (1,4) and (2,3); its 2x2 block on this pair is
+                // [[a + i s d3, i b~], [i b~*, a - i s d3]] with s = +1, b~ = b1 - i b2
+                // for (1,4) and s = -1, b~ = b1 + i b2 for (2,3).
+                const Real *rows = reinterpret_cast<const Real *>(a.rows4);
+                const Real sg = pz == 0 ? Real(1) : Real(-1);
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const int i = t + T * m;   // x_1 column of this value
+                    Real q[8];
+                    dirac4_load_row(rows + (int64_t)i * 8, q);
+                    const Real ar = q[0], b1 = q[1], b2 = q[2], d3 = sg * q[6];
+                    const C m00 = mk<C>(ar, d3), m11 = mk<C>(ar, -d3);
+                    const C m01 = mk<C>(sg * b2, b1), m10 = mk<C>(-sg * b2, b1);   // i (b1 -+ i b2)
+                    C u0 = cadd(cmul(m00, v[0][m]), cmul(m01, v[1][m]));
+                    C u1 = cadd(cmul(m10, v[0][m]), cmul(m11, v[1][m]));
+                    if (want_v) {
+                        const C vm = vph(m);
+                        u0 = Ph::apply(u0, vm);
+                        u1 = Ph::apply(u1, vm);
+                    }
+                    v[0][m] = u0;
+                    v[1][m] = u1;
+                }
+            } else if (a.op == OP_DV) {
                 // (psi_a, psi_b) <- exp(-i V tau') M (psi_a, psi_b) on this component pair
                 const double *mx = a.mix[pz];
                 const C m00 = mk<C>(Real(mx[0]), Real(mx[1])), m01 = mk<C>(Real(mx[2]), Real(mx[3]));
