@@ -587,8 +587,8 @@ def main():
                    "us_per_step": td / T1 * 1e6}
         qd.close()
         # three-dimensional four-component Dirac: 128^3 on [-4,4)^3, soft core,
-        # A with three components; 4x4 factors as streaming passes between the
-        # transforms of the four components
+        # A with three components; 4x4 factors inside four-component x and z
+        # passes, the y transforms of the four components as a batch
         n3, T3 = 128, 50
         h3 = 8.0 / n3
         X3 = wl.mesh((n3, n3, n3), (h3, h3, h3))

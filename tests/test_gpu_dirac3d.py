@@ -1,6 +1,6 @@
 """The three-dimensional four-component Dirac step on the GPU (alpha_3
-couples all components; the 4x4 factors run as streaming passes between the
-pencil transforms) against the oracle's 3D Dirac step, which the CPU tests
+couples all components; the 4x4 factors run inside four-component x and z
+passes) against the oracle's 3D Dirac step, which the CPU tests
 pin to exact free evolution with alpha_3, uniform-A convergence with all
 three components and the energy."""
 import numpy as np
