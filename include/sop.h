@@ -242,6 +242,19 @@ int sop_set_wait_limit(sop_plan plan, uint64_t wait_ns);
  * negative value turns the injection off.  Process-wide.  Returns SOP_OK. */
 int sop_debug_fail_alloc(int64_t after);
 
+/* Check builds (a debugging aid, not part of the paper's method): compiled
+ * with -DSOP_CHECK=1 (build.py with SOP_CHECK=1 in the environment writes
+ * _build_check/libsop.so), the pass kernels test their global-memory indices
+ * against the lattice, their shared-memory offsets against the tile buffer
+ * and every TMA x coordinate for 16-byte alignment; a failed test skips the
+ * access and sets bit 2 of the plan's error word, which the next
+ * synchronising call reports as SOP_ECUDA.  Every device buffer of the
+ * library is followed by 256 canary bytes, verified when it is freed.
+ * sop_debug_check_canaries stores in *bad the number of overwritten canaries
+ * (freed and live buffers) and returns SOP_OK; in a normal build it returns
+ * SOP_EUNSUPPORTED.  Synchronises the device. */
+int sop_debug_check_canaries(int64_t *bad);
+
 /* Measured FMA throughput of the current device (not part of the paper's
  * method: the denominator of the arithmetic roofline reported for the FP64
  * split step).  Runs 8 independent FMA chains per thread on 8 CTAs of 256

@@ -17,11 +17,14 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-OUT_DIR = os.path.join(HERE, "_build")
+# SOP_CHECK=1 in the environment: the check build (index and alignment tests in
+# the pass kernels, canary bytes after every device buffer) in _build_check/
+CHECK = os.environ.get("SOP_CHECK", "") == "1"
+OUT_DIR = os.path.join(HERE, "_build_check" if CHECK else "_build")
 LIB = os.path.join(OUT_DIR, "libsop.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-std=c++17", "-O3", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
-          "-Xcompiler", "-O2", f"-I{INCLUDE}", f"-I{CSRC}"]
+          "-Xcompiler", "-O2", f"-I{INCLUDE}", f"-I{CSRC}"] + (["-DSOP_CHECK=1"] if CHECK else [])
 
 # (object name, source, extra defines)
 UNITS = [

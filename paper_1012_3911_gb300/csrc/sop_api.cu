@@ -180,9 +180,32 @@ namespace {
 
 bool is_finite(double x) { return std::isfinite(x); }
 
+#ifndef SOP_CHECK
+#define SOP_CHECK 0
+#endif
+constexpr size_t kCanaryPad = 256;   // bytes after each device buffer in check builds
+
 // Allocation-failure injection (sop_debug_fail_alloc): the number of
 // device allocations still to succeed before one fails, or -1 (off).
 std::atomic<int64_t> g_fail_alloc{-1};
+
+#if SOP_CHECK
+// Check builds: every device allocation carries kCanary bytes of a fixed
+// pattern after its end, verified when the buffer is freed and by
+// sop_debug_check_canaries; a write past the end of a buffer shows there.
+constexpr size_t kCanary = kCanaryPad;
+constexpr unsigned char kCanaryByte = 0xA5;
+std::mutex g_canary_mu;
+std::map<void *, size_t> g_canary;   // buffer -> requested bytes
+std::atomic<int64_t> g_canary_bad{0};
+bool canary_intact(void *p, size_t bytes) {
+    unsigned char tail[kCanary];
+    if (cudaMemcpy(tail, static_cast<char *>(p) + bytes, kCanary, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    for (size_t i = 0; i < kCanary; ++i)
+        if (tail[i] != kCanaryByte) return false;
+    return true;
+}
+#endif
 
 template <typename T> int dalloc(T **p, size_t bytes, const char *what) {
     if (bytes == 0) bytes = 16;
@@ -190,18 +213,39 @@ template <typename T> int dalloc(T **p, size_t bytes, const char *what) {
         *p = nullptr;
         return fail(SOP_ENOMEM, std::string("cudaMalloc(") + what + "): injected allocation failure");
     }
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), bytes);
+    const size_t total = bytes + (SOP_CHECK ? kCanaryPad : 0);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), total);
     if (e != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
         return fail(e == cudaErrorMemoryAllocation ? SOP_ENOMEM : SOP_ECUDA,
                     std::string("cudaMalloc(") + what + ", " + std::to_string(bytes) + " bytes): " + cudaGetErrorString(e));
     }
+#if SOP_CHECK
+    e = cudaMemset(reinterpret_cast<char *>(*p) + bytes, kCanaryByte, kCanary);
+    if (e != cudaSuccess) return fail(SOP_ECUDA, std::string("cudaMemset(canary of ") + what + ")");
+    std::lock_guard<std::mutex> lock(g_canary_mu);
+    g_canary[reinterpret_cast<void *>(*p)] = bytes;
+#endif
     return SOP_OK;
 }
 
 void dfree(void *p) {
-    if (p) cudaFree(p);
+    if (!p) return;
+#if SOP_CHECK
+    {
+        std::lock_guard<std::mutex> lock(g_canary_mu);
+        auto it = g_canary.find(p);
+        if (it != g_canary.end()) {
+            if (!canary_intact(p, it->second)) {
+                g_canary_bad.fetch_add(1);
+                std::fprintf(stderr, "sop check: canary after a %zu-byte buffer overwritten\n", it->second);
+            }
+            g_canary.erase(it);
+        }
+    }
+#endif
+    cudaFree(p);
 }
 
 double lattice_p(int64_t n, double h, int64_t k, double hbar) {
@@ -443,8 +487,10 @@ int launch_pass(sop_plan p, const PassArgs &a0, int nc, const char *what) {
         }
     }
     cudaError_t e;
-    if (p->f64) e = contig ? launch_pass_f64_contig(a0, nc, p->stream) : launch_pass_f64_strided(a0, nc, p->stream);
-    else e = contig ? launch_pass_f32_contig(a0, nc, p->stream) : launch_pass_f32_strided(a0, nc, p->stream);
+    PassArgs a1 = a0;
+    a1.errflag = p->errflag;   // check builds record failed index tests here
+    if (p->f64) e = contig ? launch_pass_f64_contig(a1, nc, p->stream) : launch_pass_f64_strided(a1, nc, p->stream);
+    else e = contig ? launch_pass_f32_contig(a1, nc, p->stream) : launch_pass_f32_strided(a1, nc, p->stream);
     return e == cudaSuccess ? SOP_OK : cuda_fail(e, what);
 }
 
@@ -499,6 +545,8 @@ int check_errflag(sop_plan p) {
         cudaMemset(p->errflag, 0, sizeof(int));
         cudaMemset(p->tile_ctr, 0, 2 * sizeof(unsigned long long));
         p->tile_base[0] = p->tile_base[1] = 0;
+        if (h & 4)   // check builds only
+            return fail(SOP_ECUDA, "a pass kernel's bounds or alignment check failed (access skipped; SOP_CHECK build)");
         return fail(SOP_ETIMEOUT, "a pass kernel gave up waiting for its tile copies (bounded wait)");
     }
     return SOP_OK;
@@ -1538,6 +1586,21 @@ int sop_profile_read(sop_plan p, double *ms, int64_t *launches, int max_classes)
 }
 
 int64_t sop_launch_counter(sop_plan p) { return p ? p->launches : 0; }
+
+int sop_debug_check_canaries(int64_t *bad) {
+    if (!bad) return fail(SOP_EINVAL, "sop_debug_check_canaries: null output");
+#if SOP_CHECK
+    std::lock_guard<std::mutex> lock(g_canary_mu);
+    int64_t n = g_canary_bad.load();
+    for (auto &kv : g_canary)
+        if (!canary_intact(kv.first, kv.second)) ++n;
+    *bad = n;
+    return SOP_OK;
+#else
+    *bad = 0;
+    return fail(SOP_EUNSUPPORTED, "sop_debug_check_canaries: the library was built without SOP_CHECK");
+#endif
+}
 
 int sop_debug_fail_alloc(int64_t after) {
     g_fail_alloc.store(after < 0 ? -1 : after);

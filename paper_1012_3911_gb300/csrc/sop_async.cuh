@@ -466,6 +466,18 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
         if constexpr (MULTI) return reinterpret_cast<const CUtensorMap *>(d->tmap);
         else return &tmap;
     };
+    // Check builds: elements of the state array (all components) and points
+    // of one component that a tile of this launch may touch.
+    auto lat_elems = [&](const InstDesc *d) -> int64_t {
+        if constexpr (MULTI) return d->n_pencils * (int64_t)N;
+        else return (int64_t)a.n_comp_total * a.comp_stride;
+    };
+    auto lat_pts = [&](const InstDesc *d) -> int64_t {
+        if constexpr (MULTI) return d->n_pencils * (int64_t)N;
+        else return a.comp_stride;
+    };
+    (void)lat_elems;
+    (void)lat_pts;
     // Global tile g -> its lattice (null for a single lattice) and local index.
     auto locate = [&](int64_t g, int64_t &local) -> const InstDesc * {
         if constexpr (MULTI) {
@@ -523,8 +535,9 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
                 }
                 for (int c = 0; c < NC; ++c) {
                     const int64_t off = comp_index(c, bidx) * pv_i64(d, 6) + pp * N;
-                    bulk_g2s(dst0 + (uint32_t)((r * NC + c) * Cfg::PITCH * CSZ), pv_psi(d) + off, (uint32_t)(N * CSZ),
-                             bar);
+                    if (SOP_IN(a.errflag, off >= 0 && off + N <= lat_elems(d)))
+                        bulk_g2s(dst0 + (uint32_t)((r * NC + c) * Cfg::PITCH * CSZ), pv_psi(d) + off,
+                                 (uint32_t)(N * CSZ), bar);
                 }
             }
         } else {
@@ -532,6 +545,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
             const CUtensorMap *map = pv_map(d);
             tile_boxes(d, tl, [&](int c, int r, int c0, int c1, int c2, int c3) {
                 const uint32_t dst = dst0 + (uint32_t)((c * N + r * Cfg::BR) * WP * CSZ);
+                if (!SOP_IN(a.errflag, ((c0 * 8) & 15) == 0)) return;   // a TMA x must be 16-byte aligned
                 if (a.ndim == 2) tma_load_3d(dst, map, c0, c1, c3, bar);
                 else tma_load_4d(dst, map, c0, c1, c2, c3, bar);
             });
@@ -545,6 +559,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
         const uint32_t src0 = smem_addr(buf0 + b * Cfg::BUF);
         tile_boxes(d, tl, [&](int c, int r, int c0, int c1, int c2, int c3) {
             const uint32_t src = src0 + (uint32_t)((c * N + r * Cfg::BR) * WP * CSZ);
+            if (!SOP_IN(a.errflag, ((c0 * 8) & 15) == 0 && c1 >= 0 && c2 >= 0)) return;
             if (a.ndim == 2) tma_store_3d(map, c0, c1, c3, src);
             else tma_store_4d(map, c0, c1, c2, c3, src);
         });
@@ -686,7 +701,8 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
         if constexpr (VPRE) {
             if (want_v) {
 #pragma unroll
-                for (int m = 0; m < E; ++m) vpre[m] = ld_stream(vt + (t + T * m));
+                for (int m = 0; m < E; ++m)
+                    vpre[m] = SOP_IN(a.errflag, base + t + T * m < lat_pts(dp)) ? ld_stream(vt + (t + T * m)) : Ph::one();
             } else {
 #pragma unroll
                 for (int m = 0; m < E; ++m) vpre[m] = Ph::one();
@@ -694,7 +710,8 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
         }
         auto vph = [&](int m) -> C {
             if constexpr (VPRE) return vpre[m];
-            else return want_v ? ld_stream(vt + (t + T * m)) : Ph::one();
+            else return (want_v && SOP_IN(a.errflag, base + t + T * m < lat_pts(dp))) ? ld_stream(vt + (t + T * m))
+                                                                                    : Ph::one();
         };
 
         bool ok = mbar_wait_limit(b ? bar1 : bar0, Cfg::par_of(it), wait_ns, a.wait_ns > 0);
@@ -718,11 +735,17 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
             lay[c].p = row;
             if constexpr (CONTIG) {
 #pragma unroll
-                for (int m = 0; m < E; ++m) v[c][m] = row[t + T * m];
+                for (int m = 0; m < E; ++m)
+                    v[c][m] = SOP_IN(a.errflag, ((w * NC + c) * Cfg::RPITCH + t + T * m + 1) * CSZ <= (int)Cfg::BUF)
+                                  ? row[t + T * m]
+                                  : C{};
             } else {
                 const C *col = bufc + c * N * WP + w;   // TMA landing layout [c][i][w]
 #pragma unroll
-                for (int m = 0; m < E; ++m) v[c][m] = col[(t + T * m) * WP];
+                for (int m = 0; m < E; ++m)
+                    v[c][m] = SOP_IN(a.errflag, (c * N * WP + w + (t + T * m) * WP + 1) * CSZ <= (int)Cfg::BUF)
+                                  ? col[(t + T * m) * WP]
+                                  : C{};
             }
         }
         // the landing rows become exchange rows: a transform's first writes
@@ -761,7 +784,7 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
                     if (h1[0]) f1 = Ph::combine(ldg_c(h1[0] + t + T * m), f1);
                     if (h2[0]) f2 = Ph::combine(ldg_c(h2[0] + t + T * m), f2);
                     const C ps = Ph::apply(v[0][m], f1);
-                    if (active) st_stream(mo + T * m, ps);
+                    if (active && SOP_IN(a.errflag, coff[0] + base + t + T * m < lat_elems(dp))) st_stream(mo + T * m, ps);
                     v[0][m] = Ph::apply(ps, f2);
                 }
             }
@@ -905,7 +928,8 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
                 for (int c = 0; c < NC; ++c) {
                     C *dst = pv_psi(dp) + coff[c] + base + t;
 #pragma unroll
-                    for (int m = 0; m < E; ++m) st_stream(dst + T * m, v[c][m]);
+                    for (int m = 0; m < E; ++m)
+                        if (SOP_IN(a.errflag, coff[c] + base + t + T * m < lat_elems(dp))) st_stream(dst + T * m, v[c][m]);
                 }
             }
             if constexpr (!Cfg::SINGLE) __syncthreads();   // the tile buffer is free again; s_tile is set
@@ -917,7 +941,9 @@ __global__ void __launch_bounds__(AsyncCfg<Real, N, NC, CONTIG, VAR>::THREADS, A
             for (int c = 0; c < NC; ++c) {
                 C *col = bufc + c * N * WP + w;
 #pragma unroll
-                for (int m = 0; m < E; ++m) col[(t + T * m) * WP] = v[c][m];
+                for (int m = 0; m < E; ++m)
+                    if (SOP_IN(a.errflag, (c * N * WP + w + (t + T * m) * WP + 1) * CSZ <= (int)Cfg::BUF))
+                        col[(t + T * m) * WP] = v[c][m];
             }
             fence_proxy_async_smem();   // make these writes visible to the bulk copy engine
             if (Cfg::SINGLE && tid == 0) publish_next();

@@ -103,6 +103,22 @@ __device__ __forceinline__ void unravel3(int64_t lin, const int64_t *dims, int n
 // per-point tables stream through each pass once and must not push the
 // twiddle and field tables out of L1, while psi should stay in L2 for the
 // next pass.
+// Check builds (-DSOP_CHECK=1): SOP_IN(flag, cond) is cond, and a false cond
+// sets bit 2 of the error word at flag so the caller can skip the access; in
+// normal builds it is the constant true and cond is not evaluated.
+#ifndef SOP_CHECK
+#define SOP_CHECK 0
+#endif
+__device__ __forceinline__ bool sop_in(int *flag, bool cond) {
+    if (!cond && flag) atomicOr(flag, 4);
+    return cond;
+}
+#if SOP_CHECK
+#define SOP_IN(flag, cond) sop_in((flag), (cond))
+#else
+#define SOP_IN(flag, cond) true
+#endif
+
 template <typename C> __device__ __forceinline__ C ld_stream(const C *p) { return __ldcg(p); }
 template <typename C> __device__ __forceinline__ void st_stream(C *p, C v) { __stcg(p, v); }
 
@@ -178,6 +194,7 @@ __device__ __forceinline__ void apply_op(cplx_t<Real> (&v)[NC][E], const PassArg
                 const int i = t + T * m;
                 const int64_t k = base + (int64_t)i * stride;
                 C q0, q1;
+                if (!SOP_IN(a.errflag, k >= 0 && k < a.comp_stride)) continue;
                 if constexpr (sizeof(Real) == 4) {
                     const float4 q = __ldcg(reinterpret_cast<const float4 *>(dt2) + k);
                     q0 = mk<C>(q.x, q.y);
@@ -241,6 +258,7 @@ __device__ __forceinline__ void apply_op4(cplx_t<Real> (&v)[4][E], const PassArg
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int64_t k = base + (int64_t)(t + T * m) * stride;
+            if (!SOP_IN(a.errflag, k >= 0 && k < a.comp_stride)) continue;
             Real co, sm, sx, sy, sz;
             dirac4_load_kin(tab, k, co, sm, sx, sy, sz);
             const C x[4] = {v[0][m], v[1][m], v[2][m], v[3][m]};

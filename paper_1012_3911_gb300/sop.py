@@ -20,7 +20,8 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libsop.so")
+# SOP_CHECK=1: the check build (see build.py)
+LIB_PATH = os.path.join(_HERE, "_build_check" if os.environ.get("SOP_CHECK", "") == "1" else "_build", "libsop.so")
 
 SOP_C64, SOP_C128 = 0, 1
 SOP_OK, SOP_EINVAL, SOP_EUNSUPPORTED, SOP_ENOMEM, SOP_ECUDA, SOP_ETIMEOUT, SOP_ESTATE = 0, -1, -2, -3, -4, -5, -6
@@ -236,6 +237,18 @@ def sop_fma_peak(f64: bool = True, stream=None) -> float:
     out = ctypes.c_double()
     _check(fn(1 if f64 else 0, ctypes.byref(out), _stream_handle(stream)))
     return out.value
+
+
+def sop_debug_check_canaries() -> int:
+    """Check builds: the number of overwritten canaries after device buffers
+    (SopError SOP_EUNSUPPORTED in a normal build)."""
+    lib = load()
+    fn = lib.sop_debug_check_canaries
+    fn.argtypes = [ctypes.POINTER(ctypes.c_int64)]
+    fn.restype = ctypes.c_int
+    bad = ctypes.c_int64(0)
+    _check(fn(ctypes.byref(bad)))
+    return int(bad.value)
 
 
 def sop_debug_fail_alloc(after: int) -> None:

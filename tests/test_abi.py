@@ -96,3 +96,18 @@ def test_noalloc_wrapper_rejects_unsafe_tensors():
     out = torch.zeros(1, dtype=torch.float64)
     with pytest.raises(ValueError):
         sop.sop_norm_noalloc(cpu, 16, sop.SOP_C64, 1.0, out)   # not a CUDA tensor
+
+
+def test_canary_check_is_a_check_build_entry_point():
+    """sop_debug_check_canaries answers SOP_EUNSUPPORTED in a normal build
+    (no GPU call) and rejects a null output pointer."""
+    import os
+    if os.environ.get("SOP_CHECK", "") == "1":
+        pytest.skip("check build selected")
+    lib = sop.load()
+    lib.sop_debug_check_canaries.argtypes = [ctypes.c_void_p]
+    lib.sop_debug_check_canaries.restype = ctypes.c_int
+    assert lib.sop_debug_check_canaries(None) == sop.SOP_EINVAL
+    with pytest.raises(sop.SopError) as ei:
+        sop.sop_debug_check_canaries()
+    assert ei.value.status == sop.SOP_EUNSUPPORTED
