@@ -1650,14 +1650,17 @@ int sop_autotune(sop_plan p, double dt, int trial_steps, int *chosen) {
         if (!model.empty() && !loaded.count(once)) {
             loaded.insert(once);
             if (FILE *f = std::fopen(cache_file, "r")) {
-                char name[256];
+                char line[512], name[256];
                 long long v[7];
                 int c0, c1;
-                while (std::fscanf(f, "%255s %lld %lld %lld %lld %lld %lld %d %d", name, &v[0], &v[1], &v[2], &v[3],
-                                   &v[4], &v[5], &c0, &c1) == 9)
+                while (std::fgets(line, sizeof(line), f)) {   // malformed lines are skipped
+                    if (std::sscanf(line, "%255s %lld %lld %lld %lld %lld %lld %d %d", name, &v[0], &v[1], &v[2],
+                                    &v[3], &v[4], &v[5], &c0, &c1) != 9)
+                        continue;
                     if (model == name && c0 >= 0 && c0 < kPassVariants && c1 >= 0 && c1 < kPassVariants &&
                         (v[5] == 0 || (c0 == 0 && c1 == 0)))   // complex128 has shape 0 only
                         cache[{p->device, v[0], v[1], v[2], v[3], v[4], v[5]}] = {c0, c1};
+                }
                 std::fclose(f);
             }
         }

@@ -80,8 +80,10 @@ def test_autotune_cache_file_is_read_and_appended(tmp_path, monkeypatch):
     model = torch.cuda.get_device_name(0).replace(" ", "_")
     path = tmp_path / "shapes.txt"
     # 2D 192 x 96 complex64 (sides no other test tunes) -> shapes 3 and 5;
-    # a complex128 line with shapes other than 0 is ignored
-    path.write_text(f"{model} 2 192 96 1 1 0 3 5\n{model} 2 192 96 1 1 1 4 4\nother_gpu 2 96 192 1 1 0 2 2\n")
+    # a complex128 line with shapes other than 0 is ignored, so are malformed
+    # lines and other models' lines
+    path.write_text(f"a malformed line\n{model} 2 192 96 1 1 0 3 5\n{model} 2 192 96 1 1 1 4 4\n"
+                    f"other_gpu 2 96 192 1 1 0 2 2\n")
     monkeypatch.setenv("SOP_AUTOTUNE_CACHE", str(path))
     w = gc.random_workload((192, 96), 1, seed=5, n_steps=2, dt=0.01, field_scale=0.05)
     prop = sop.Propagator(w.dims, w.spacing, 1, "c64")
