@@ -589,17 +589,12 @@ def main():
         # three-dimensional four-component Dirac: 128^3 on [-4,4)^3, soft core,
         # A with three components; 4x4 factors inside four-component x and z
         # passes, the y transforms of the four components as a batch
-        n3, T3 = 128, 50
-        h3 = 8.0 / n3
-        X3 = wl.mesh((n3, n3, n3), (h3, h3, h3))
-        t3 = (np.arange(T3) + 0.5) * 1e-4
-        A3 = np.stack([20.0 * np.cos(2.0 * t3), 5.0 * np.sin(2.0 * t3), 2.0 * np.ones_like(t3)], axis=1)
-        scal = wl.gaussian((n3, n3, n3), (h3, h3, h3), (0.0, 0.0, 0.0), 0.5, (50.0, 0.0, 0.0))
-        psi3 = wl.dirac_positive_spin_up(scal, (n3, n3, n3), (h3, h3, h3))
-        q3 = sop.Propagator((n3, n3, n3), (h3, h3, h3), 4, "c64")
-        q3.set_potential(-1.0 / np.sqrt(X3[0] ** 2 + X3[1] ** 2 + X3[2] ** 2 + 0.01))
-        q3.set_state(torch.from_numpy(psi3))
-        del X3, scal, psi3
+        w3 = wl.dirac3d_packet(128, 50)
+        n3, T3, A3 = w3.dims[0], w3.n_steps, w3.field
+        q3 = sop.Propagator(w3.dims, w3.spacing, 4, "c64")
+        q3.set_potential(w3.V)
+        q3.set_state(torch.from_numpy(w3.psi0))
+        del w3
         q3.step(3, 1e-4, A3[:3])
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -626,14 +621,9 @@ def main():
         # 2D Dirac in a pulse travelling along x (A_y(x, t), the paper's
         # scattering geometry) on the 1024^2 Dirac lattice, against the same
         # plan with the uniform field of that workload
-        w4 = wl.config4(n_steps=200)
-        n4, T4 = w4.dims[0], w4.n_steps
-        x4 = wl.lattice(n4, w4.spacing[0])
-        kx = 2 * np.pi / (n4 * w4.spacing[0])
-        t4 = (np.arange(T4) + 0.5) * w4.dt
-        eta = kx * x4[None, :] - 137.036 * kx * t4[:, None]
-        A4 = np.zeros((T4, n4, 2))
-        A4[:, :, 1] = 20.0 * np.sin(eta) * np.sin(0.5 * eta) ** 2
+        w4 = wl.dirac_pulse(200)
+        n4, T4, A4 = w4.dims[0], w4.n_steps, w4.field
+        w4.field = wl.config4(n_steps=200).field   # the uniform field of the same workload
         qp = sop.Propagator(w4.dims, w4.spacing, 4, "c64")
         qp.set_potential(w4.V)
         qp.set_state(torch.from_numpy(w4.psi0))

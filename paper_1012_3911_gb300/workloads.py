@@ -251,6 +251,37 @@ def config4(n: int = 1024, L: float = 8.0, dt: float = 1e-4, n_steps: int = 1000
                     dt, n_steps, field, meta=dict(A0=A0, omega=omega, T=T, L=L, p0=list(p0)))
 
 
+def dirac3d_packet(n: int = 128, n_steps: int = 50, dt: float = 1e-4) -> Workload:
+    """3D four-component Dirac on [-4, 4)^3: soft core V = -1/sqrt(r^2 + 0.01),
+    uniform A(t) = (20 cos 2t, 5 sin 2t, 2) at the step midpoints, and a
+    positive-energy spin-up packet (Gaussian sigma 0.5, p0 = (50, 0, 0)) at the
+    origin."""
+    h = 8.0 / n
+    dims, sp = (n, n, n), (h, h, h)
+    X = mesh(dims, sp)
+    t = (np.arange(n_steps) + 0.5) * dt
+    A = np.stack([20.0 * np.cos(2.0 * t), 5.0 * np.sin(2.0 * t), 2.0 * np.ones_like(t)], axis=1)
+    psi0 = dirac_positive_spin_up(gaussian(dims, sp, (0.0, 0.0, 0.0), 0.5, (50.0, 0.0, 0.0)), dims, sp)
+    V = -1.0 / np.sqrt(X[0] ** 2 + X[1] ** 2 + X[2] ** 2 + 0.01)
+    return Workload("3d_dirac_packet", dims, sp, 4, psi0, V, dt, n_steps, A)
+
+
+def dirac_pulse(n_steps: int = 200) -> Workload:
+    """The 2D Dirac lattice, potential and packet of config 4 in a pulse
+    travelling along x: A_y(x, t) = 20 sin(eta) sin^2(eta/2) with
+    eta = k x - c k t, k = 2 pi / L, sampled at the step midpoints on every
+    lattice column; field shape (n_steps, n_x, 2) (meta['profile'] = True)."""
+    w = config4(n_steps=n_steps)
+    n = w.dims[0]
+    x = lattice(n, w.spacing[0])
+    k = 2 * np.pi / (n * w.spacing[0])
+    t = (np.arange(n_steps) + 0.5) * w.dt
+    eta = k * x[None, :] - 137.036 * k * t[:, None]
+    A = np.zeros((n_steps, n, 2))
+    A[:, :, 1] = 20.0 * np.sin(eta) * np.sin(0.5 * eta) ** 2
+    return Workload("2d_dirac_pulse", w.dims, w.spacing, 4, w.psi0, w.V, w.dt, n_steps, A, meta=dict(profile=True))
+
+
 CONFIG5_SIDES = (256, 384, 512, 768, 1024, 1536, 2048)
 
 

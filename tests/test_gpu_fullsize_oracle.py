@@ -86,3 +86,40 @@ def test_full_size_full_length_against_the_oracle(cfg, dtype):
         assert abs(energy - float(g["energy"])) < 1e-10 * max(1.0, abs(float(g["energy"])))
     else:
         assert abs(norm - float(g["norm"])) < 2e-4
+
+
+# The benchmark's follow-on Dirac workloads at their full size and step count
+# (3D four-component packet, 128^3 x 50 steps; 2D Dirac in a pulse with A
+# varying along x, 1024^2 x 200 steps), against the oracle's stored samples.
+EXTRA = {"dirac3d": wl.dirac3d_packet, "pulse": wl.dirac_pulse}
+
+
+def extra_fixture(name):
+    g = np.load(os.path.join(GOLDEN, f"fullsize_{name}.npz"))
+    w = EXTRA[name]()
+    assert tuple(g["dims"]) == w.dims and int(g["n_steps"]) == w.n_steps and float(g["dt"]) == w.dt
+    assert abs(float(g["psi0_abs2"]) - float(np.sum(np.abs(w.psi0) ** 2))) <= 1e-9 * float(g["psi0_abs2"])
+    assert abs(float(g["V_sum"]) - float(w.V.sum())) <= 1e-9 * abs(float(g["V_sum"]))
+    assert abs(float(g["field_sum"]) - float(np.asarray(w.field).sum())) <= 1e-9 * max(1.0, abs(float(g["field_sum"])))
+    return g, w
+
+
+@pytest.mark.parametrize("name", ["dirac3d", "pulse"])
+def test_follow_on_dirac_workloads_full_size_against_the_oracle(name):
+    g, w = extra_fixture(name)
+    prop = sop.Propagator(w.dims, w.spacing, w.comps, "c64",
+                          params=dict(mass=w.mass, charge=w.charge, hbar=w.hbar, c=w.c))
+    if w.meta.get("profile"):
+        prop.set_field_profile(True)
+    prop.set_state(torch.from_numpy(w.psi0))
+    prop.set_potential(w.V)
+    prop.step(w.n_steps, w.dt, w.field)
+    torch.cuda.synchronize()
+    idx = torch.from_numpy(g["idx"]).cuda()
+    got = prop.state.reshape(-1)[idx].to(torch.complex128).cpu().numpy()
+    err = gc.relerr(got, g["values"])
+    norm = prop.norm()
+    prop.close()
+    print(f"{name} c64: sampled relL2 {err:.3e}, norm {norm:.12f} (oracle {float(g['norm']):.12f})")
+    assert err < gc.TOL_F32_FULL, err
+    assert abs(norm - float(g["norm"])) < 2e-4
