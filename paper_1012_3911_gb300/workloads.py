@@ -282,6 +282,16 @@ def dirac_pulse(n_steps: int = 200) -> Workload:
     return Workload("2d_dirac_pulse", w.dims, w.spacing, 4, w.psi0, w.V, w.dt, n_steps, A, meta=dict(profile=True))
 
 
+def velocity_gauge_benchmark() -> Workload:
+    """The benchmark workload (config 2) in the velocity gauge: the field
+    samples become the vector potential A_n = -dt sum_{m <= n} E_m (so that
+    E = -dA/dt), entering the momentum-space factor (meta['gauge'])."""
+    w = config2()
+    A = -np.cumsum(w.field, axis=0) * w.dt
+    return Workload("2d_schrodinger_velocity_gauge", w.dims, w.spacing, 1, w.psi0, w.V, w.dt, w.n_steps, A,
+                    meta=dict(w.meta, gauge="velocity"))
+
+
 CONFIG5_SIDES = (256, 384, 512, 768, 1024, 1536, 2048)
 
 

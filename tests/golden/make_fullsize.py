@@ -1,11 +1,12 @@
 """Write the full-size, full-length oracle fixtures ``fullsize_config{2,3,4}.npz``
-and ``fullsize_{dirac3d,pulse}.npz``.
+and ``fullsize_{dirac3d,pulse,velocity}.npz``.
 
 Each fixture holds the FP64 oracle's final state of one workload
 (``paper_1012_3911_gb300.workloads.config2/3/4`` at their full lattice and full
 step count: 2048^2 x 5000 steps, 512^3 x 200 steps, 1024^2 Dirac x 1000 steps;
 and the benchmark's follow-on Dirac workloads ``dirac3d_packet``, 128^3 x 50
-steps, and ``dirac_pulse``, 1024^2 x 200 steps with A varying along x) on a
+steps, ``dirac_pulse``, 1024^2 x 200 steps with A varying along x, and
+``velocity_gauge_benchmark``, config 2 in the velocity gauge) on a
 seeded sample of lattice values, plus the oracle's norm and field-free energy
 of that final state and a few checksums of the inputs.  The GPU parity tests
 (``tests/test_gpu_fullsize_oracle.py``) propagate the same inputs at full size
@@ -19,7 +20,7 @@ probability proportional to |psi_N|^2 (where the wave function lives), from
 Only the oracle and the seeded input generators run here; nothing of the CUDA
 path.  Run from the repository root (it takes about 75 minutes on 8 cores):
 
-    python tests/golden/make_fullsize.py [2 3 4 dirac3d pulse]
+    python tests/golden/make_fullsize.py [2 3 4 dirac3d pulse velocity]
 """
 from __future__ import annotations
 
@@ -57,7 +58,8 @@ def sample_indices(psi: np.ndarray, seed: int) -> np.ndarray:
 
 
 # follow-on workloads: generator and sample seed
-EXTRA = {"dirac3d": (wl.dirac3d_packet, 2005), "pulse": (wl.dirac_pulse, 2006)}
+EXTRA = {"dirac3d": (wl.dirac3d_packet, 2005), "pulse": (wl.dirac_pulse, 2006),
+         "velocity": (wl.velocity_gauge_benchmark, 2007)}
 
 
 def workload(cfg) -> wl.Workload:
@@ -73,7 +75,7 @@ def run(cfg) -> str:
     t0 = time.time()
     if w.comps == 1:
         out = oracle.schrodinger_propagate(w.psi0, w.V, w.spacing, w.dt, w.n_steps, w.field,
-                                           w.mass, w.charge, w.hbar)
+                                           w.mass, w.charge, w.hbar, gauge=w.meta.get("gauge", "length"))
     elif w.meta.get("profile"):
         out = oracle.dirac_propagate_profile(w.psi0, w.V, w.spacing, w.dt, w.n_steps, w.field,
                                              w.mass, w.charge, w.hbar, w.c)
@@ -99,7 +101,7 @@ def run(cfg) -> str:
 
 def main(argv):
     oracle.set_threads(oracle.max_threads())
-    cfgs = [a if a in EXTRA else int(a) for a in argv] or [4, 2, 3, "dirac3d", "pulse"]
+    cfgs = [a if a in EXTRA else int(a) for a in argv] or [4, 2, 3, "dirac3d", "pulse", "velocity"]
     for c in cfgs:
         run(c)
 

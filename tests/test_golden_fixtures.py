@@ -18,6 +18,7 @@ CASES = {
     "config4": wl.config4,
     "dirac3d": wl.dirac3d_packet,
     "pulse": wl.dirac_pulse,
+    "velocity": wl.velocity_gauge_benchmark,
 }
 
 

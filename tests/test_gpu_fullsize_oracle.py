@@ -88,10 +88,11 @@ def test_full_size_full_length_against_the_oracle(cfg, dtype):
         assert abs(norm - float(g["norm"])) < 2e-4
 
 
-# The benchmark's follow-on Dirac workloads at their full size and step count
-# (3D four-component packet, 128^3 x 50 steps; 2D Dirac in a pulse with A
-# varying along x, 1024^2 x 200 steps), against the oracle's stored samples.
-EXTRA = {"dirac3d": wl.dirac3d_packet, "pulse": wl.dirac_pulse}
+# The benchmark's follow-on workloads at their full size and step count (3D
+# four-component Dirac packet, 128^3 x 50 steps; 2D Dirac in a pulse with A
+# varying along x, 1024^2 x 200 steps; the benchmark lattice in the velocity
+# gauge, 2048^2 x 5000 steps), against the oracle's stored samples.
+EXTRA = {"dirac3d": wl.dirac3d_packet, "pulse": wl.dirac_pulse, "velocity": wl.velocity_gauge_benchmark}
 
 
 def extra_fixture(name):
@@ -104,13 +105,15 @@ def extra_fixture(name):
     return g, w
 
 
-@pytest.mark.parametrize("name", ["dirac3d", "pulse"])
-def test_follow_on_dirac_workloads_full_size_against_the_oracle(name):
+@pytest.mark.parametrize("name", ["dirac3d", "pulse", "velocity"])
+def test_follow_on_workloads_full_size_against_the_oracle(name):
     g, w = extra_fixture(name)
     prop = sop.Propagator(w.dims, w.spacing, w.comps, "c64",
                           params=dict(mass=w.mass, charge=w.charge, hbar=w.hbar, c=w.c))
     if w.meta.get("profile"):
         prop.set_field_profile(True)
+    if w.meta.get("gauge") == "velocity":
+        prop.set_gauge("velocity")
     prop.set_state(torch.from_numpy(w.psi0))
     prop.set_potential(w.V)
     prop.step(w.n_steps, w.dt, w.field)
